@@ -1,0 +1,640 @@
+/*
+ * FP64 CPU oracle for the overlap-operator hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: it exists so the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark can check the CUDA library against a plain, slow,
+ * obviously correct restatement of the method.  It shares no code, header,
+ * table or constant with the CUDA path.
+ *
+ * Everything is double precision, canonical (non even/odd) layout:
+ *   gauge  U   : complex [Lt][Lz][Ly][Lx][mu=0..3 (x,y,z,t)][3][3]
+ *   spinor psi : complex [Lt][Lz][Ly][Lx][spin 4][colour 3]
+ * dims[] = {Lx, Ly, Lz, Lt}; bc[mu] is a real phase (+1 periodic, -1
+ * antiperiodic) multiplying every hop that crosses the boundary in mu.
+ *
+ * Gamma matrices: Euclidean chiral basis, gamma_k = [[0,-i s_k],[i s_k,0]]
+ * (k=1,2,3), gamma_4 = [[0,1],[1,0]], gamma_5 = g1 g2 g3 g4 = diag(1,1,-1,-1).
+ * The paper fixes only "chiral" (Sec. V); the explicit matrices are this
+ * project's reading.
+ *
+ * Parity status of each function (what pins it) is listed in the Python
+ * wrapper oracle/__init__.py.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* gamma matrices                                                       */
+/* ------------------------------------------------------------------ */
+static cplx G[5][4][4]; /* G[0..3] = gamma_1..gamma_4, G[4] = gamma_5 */
+static int g_ready = 0;
+
+static void init_gamma(void)
+{
+    if (g_ready) return;
+    cplx sig[3][2][2] = {{{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+    memset(G, 0, sizeof(G));
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                G[k][a][2 + b] = -I * sig[k][a][b];
+                G[k][2 + a][b] = I * sig[k][a][b];
+            }
+    for (int a = 0; a < 2; ++a) {
+        G[3][a][2 + a] = 1;
+        G[3][2 + a][a] = 1;
+    }
+    /* gamma_5 as the product g1 g2 g3 g4 (checked to be diag(1,1,-1,-1) by the tests) */
+    cplx t1[4][4], t2[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 4; ++k) s += G[0][i][k] * G[1][k][j];
+            t1[i][j] = s;
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 4; ++k) s += t1[i][k] * G[2][k][j];
+            t2[i][j] = s;
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 4; ++k) s += t2[i][k] * G[3][k][j];
+            G[4][i][j] = s;
+        }
+    g_ready = 1;
+}
+
+/* gamma matrix mu (0..3 = gamma_1..gamma_4, 4 = gamma_5), row-major 4x4 */
+void or_gamma(int mu, cplx *out)
+{
+    init_gamma();
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) out[4 * i + j] = G[mu][i][j];
+}
+
+/* ------------------------------------------------------------------ */
+/* lattice helpers                                                      */
+/* ------------------------------------------------------------------ */
+static long volume(const int *d) { return (long)d[0] * d[1] * d[2] * d[3]; }
+
+static void coords(const int *d, long n, int c[4])
+{
+    c[0] = (int)(n % d[0]);
+    n /= d[0];
+    c[1] = (int)(n % d[1]);
+    n /= d[1];
+    c[2] = (int)(n % d[2]);
+    c[3] = (int)(n / d[2]);
+}
+
+static long index_of(const int *d, const int c[4])
+{
+    return ((long)(c[3] * d[2] + c[2]) * d[1] + c[1]) * d[0] + c[0];
+}
+
+/* neighbour n + step*mu_hat (step = +1 or -1) and the boundary phase of the hop */
+static long neighbour(const int *d, const double *bc, long n, int mu, int step, double *phase)
+{
+    int c[4];
+    coords(d, n, c);
+    *phase = 1.0;
+    c[mu] += step;
+    if (c[mu] == d[mu]) {
+        c[mu] = 0;
+        *phase = bc[mu];
+    } else if (c[mu] < 0) {
+        c[mu] = d[mu] - 1;
+        *phase = bc[mu];
+    }
+    return index_of(d, c);
+}
+
+/* ------------------------------------------------------------------ */
+/* Wilson operator, Eqs. (1)-(2)                                        */
+/* ------------------------------------------------------------------ */
+/* (T_mu psi)_n for one site, accumulated into acc[4][3]:
+ *   mu > 0 : U_mu(n)            (1 - gamma_mu) psi_{n+mu}
+ *   mu < 0 : U_mu(n-mu)^dagger  (1 + gamma_mu) psi_{n-mu}
+ * The spin matrix acts on the spin index, the link on the colour index. */
+static void hop_site(const int *d, const double *bc, const cplx *U, const cplx *in, long n,
+                     cplx acc[4][3])
+{
+    for (int s = 0; s < 4; ++s)
+        for (int a = 0; a < 3; ++a) acc[s][a] = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        for (int dir = 0; dir < 2; ++dir) {
+            int step = dir == 0 ? +1 : -1;
+            double ph;
+            long m = neighbour(d, bc, n, mu, step, &ph);
+            /* spin matrix 1 -/+ gamma_mu */
+            cplx P[4][4];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    P[i][j] = (i == j ? 1.0 : 0.0) - (double)step * G[mu][i][j];
+            /* link: U_mu(n) forward, U_mu(n-mu)^dagger backward */
+            cplx L[3][3];
+            const cplx *u = step > 0 ? U + (n * 4 + mu) * 9 : U + (m * 4 + mu) * 9;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) L[a][b] = step > 0 ? u[3 * a + b] : conj(u[3 * b + a]);
+            const cplx *p = in + m * 12;
+            for (int s = 0; s < 4; ++s) {
+                cplx chi[3];
+                for (int b = 0; b < 3; ++b) {
+                    cplx v = 0;
+                    for (int t = 0; t < 4; ++t) v += P[s][t] * p[3 * t + b];
+                    chi[b] = v;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    cplx v = 0;
+                    for (int b = 0; b < 3; ++b) v += L[a][b] * chi[b];
+                    acc[s][a] += ph * v;
+                }
+            }
+        }
+    }
+}
+
+/* out = D_w(m) in = (m + 4) in - 1/2 sum_{mu=+-1..+-4} T_mu in       (Eq. 1) */
+void or_dslash(const int *d, const double *bc, const cplx *U, double m, const cplx *in, cplx *out)
+{
+    init_gamma();
+    long V = volume(d);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < V; ++n) {
+        cplx acc[4][3];
+        hop_site(d, bc, U, in, n, acc);
+        for (int s = 0; s < 4; ++s)
+            for (int a = 0; a < 3; ++a)
+                out[n * 12 + 3 * s + a] = (m + 4.0) * in[n * 12 + 3 * s + a] - 0.5 * acc[s][a];
+    }
+}
+
+/* D_w(m) in at a list of sites only: out[k][12] = (D_w in)(sites[k]) */
+void or_dslash_sites(const int *d, const double *bc, const cplx *U, double m, const cplx *in,
+                     long nsites, const long *sites, cplx *out)
+{
+    init_gamma();
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < nsites; ++k) {
+        long n = sites[k];
+        cplx acc[4][3];
+        hop_site(d, bc, U, in, n, acc);
+        for (int s = 0; s < 4; ++s)
+            for (int a = 0; a < 3; ++a)
+                out[k * 12 + 3 * s + a] = (m + 4.0) * in[n * 12 + 3 * s + a] - 0.5 * acc[s][a];
+    }
+}
+
+/* out = gamma_5 in, by the explicit 4x4 matrix */
+void or_gamma5(long nsites, const cplx *in, cplx *out)
+{
+    init_gamma();
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < nsites; ++n) {
+        cplx tmp[12];
+        for (int s = 0; s < 4; ++s)
+            for (int a = 0; a < 3; ++a) {
+                cplx v = 0;
+                for (int t = 0; t < 4; ++t) v += G[4][s][t] * in[n * 12 + 3 * t + a];
+                tmp[3 * s + a] = v;
+            }
+        memcpy(out + n * 12, tmp, sizeof(tmp));
+    }
+}
+
+/* H_w = gamma_5 D_w(m)   (Sec. II: H_w is hermitian by gamma_5-hermiticity) */
+void or_hw(const int *d, const double *bc, const cplx *U, double m, const cplx *in, cplx *out)
+{
+    or_dslash(d, bc, U, m, in, out);
+    or_gamma5(volume(d), out, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* level-1 vector helpers (plain loops)                                 */
+/* ------------------------------------------------------------------ */
+static cplx vdot(long N, const cplx *a, const cplx *b) /* a^dagger b */
+{
+    double re = 0, im = 0;
+#pragma omp parallel for reduction(+ : re, im) schedule(static)
+    for (long i = 0; i < N; ++i) {
+        cplx v = conj(a[i]) * b[i];
+        re += creal(v);
+        im += cimag(v);
+    }
+    return re + I * im;
+}
+
+static double vnorm2(long N, const cplx *a) { return creal(vdot(N, a, a)); }
+
+/* ------------------------------------------------------------------ */
+/* polynomial approximation P(x) ~ x^{-1/2} on [eps, 1], Eq. (4)        */
+/* ------------------------------------------------------------------ */
+/* Coefficients of the degree-n Chebyshev interpolant of x^{-1/2} on
+ * [eps, 1] in the variable y = (2x - (1+eps)) / (1-eps):
+ *   P(x) = sum_{k=0}^{n} c_k T_k(y),
+ * interpolating at the n+1 Chebyshev nodes y_j = cos(pi (j+1/2)/(n+1)).
+ * c[0] is returned already halved, so the sum above is plain. */
+void or_cheb_coeffs(double eps, int n, double *c)
+{
+    int np = n + 1;
+    double *f = malloc(sizeof(double) * np);
+    for (int j = 0; j < np; ++j) {
+        double th = M_PI * (j + 0.5) / np;
+        double x = 0.5 * (1.0 + eps) + 0.5 * (1.0 - eps) * cos(th);
+        f[j] = 1.0 / sqrt(x);
+    }
+    for (int k = 0; k <= n; ++k) {
+        double s = 0;
+        for (int j = 0; j < np; ++j) s += f[j] * cos(k * M_PI * (j + 0.5) / np);
+        c[k] = 2.0 * s / np;
+    }
+    c[0] *= 0.5;
+    free(f);
+}
+
+/* P(x) by Clenshaw's recurrence (the scalar form of Sec. V's recursion) */
+double or_poly_eval(const double *c, int n, double eps, double x)
+{
+    double y = (2.0 * x - (1.0 + eps)) / (1.0 - eps);
+    double b1 = 0, b2 = 0;
+    for (int k = n; k >= 1; --k) {
+        double b0 = c[k] + 2.0 * y * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+    }
+    return c[0] + y * b1 - b2;
+}
+
+/* delta = max_{x in [eps,1]} |1 - sqrt(x) P(x)| on npts log-spaced points (Eq. 4) */
+double or_poly_delta(const double *c, int n, double eps, int npts)
+{
+    double dmax = 0;
+    for (int i = 0; i < npts; ++i) {
+        double x = exp(log(eps) + (log(1.0) - log(eps)) * i / (double)(npts - 1));
+        double e = fabs(1.0 - sqrt(x) * or_poly_eval(c, n, eps, x));
+        if (e > dmax) dmax = e;
+    }
+    return dmax;
+}
+
+/* ------------------------------------------------------------------ */
+/* sign(H_w) with low-mode deflation, Eqs. (5)-(7)                      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const int *d;
+    const double *bc;
+    const cplx *U;
+    double mw;      /* Wilson mass inside H_w */
+    double lmax;    /* ||H_w|| estimate: Q = H_w / lmax */
+    double eps;
+    int n;
+    const double *c;
+    int nev;
+    const double *lam; /* eigenvalues of H_w (signed) */
+    const cplx *eta;   /* eigenvectors [nev][12V], orthonormal */
+} sign_args;
+
+/* out = Y in, with Y = (2 Q^2 - (1+eps)) / (1-eps), Q = H_w / lmax */
+static void apply_Y(const sign_args *a, const cplx *in, cplx *out, cplx *tmp)
+{
+    long N = 12 * volume(a->d);
+    or_hw(a->d, a->bc, a->U, a->mw, in, tmp);
+    or_hw(a->d, a->bc, a->U, a->mw, tmp, out);
+    double s = 2.0 / (a->lmax * a->lmax * (1.0 - a->eps));
+    double t = (1.0 + a->eps) / (1.0 - a->eps);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) out[i] = s * out[i] - t * in[i];
+}
+
+/* sign(H_w) in ~ sum_i sign(lam_i) (eta_i^dag in) eta_i + Q P(Q^2) (1 - P_l) in   (Eq. 7) */
+static void sign_apply(const sign_args *a, const cplx *in, cplx *out)
+{
+    long N = 12 * volume(a->d);
+    cplx *ph = malloc(sizeof(cplx) * N);
+    cplx *b1 = calloc(N, sizeof(cplx));
+    cplx *b2 = calloc(N, sizeof(cplx));
+    cplx *y = malloc(sizeof(cplx) * N);
+    cplx *tmp = malloc(sizeof(cplx) * N);
+    cplx *proj = malloc(sizeof(cplx) * (a->nev > 0 ? a->nev : 1));
+
+    /* psi_h = psi - sum_i eta_i (eta_i^dag psi)    (Eq. 6) */
+    memcpy(ph, in, sizeof(cplx) * N);
+    for (int i = 0; i < a->nev; ++i) {
+        const cplx *e = a->eta + (long)i * N;
+        proj[i] = vdot(N, e, in);
+        for (long k = 0; k < N; ++k) ph[k] -= proj[i] * e[k];
+    }
+
+    /* Clenshaw: b_k = c_k psi_h + 2 Y b_{k+1} - b_{k+2}, k = n..1;
+       P psi_h = c_0 psi_h + Y b_1 - b_2                            (Sec. V) */
+    for (long k = 0; k < N; ++k) b1[k] = a->c[a->n] * ph[k]; /* b_n (b_{n+1} = 0) */
+    for (int k = a->n - 1; k >= 1; --k) {
+        apply_Y(a, b1, y, tmp);
+        for (long i = 0; i < N; ++i) {
+            cplx b0 = a->c[k] * ph[i] + 2.0 * y[i] - b2[i];
+            b2[i] = b1[i];
+            b1[i] = b0;
+        }
+    }
+    cplx *pp = y; /* P(Q^2) psi_h */
+    if (a->n >= 1) {
+        apply_Y(a, b1, y, tmp);
+        for (long i = 0; i < N; ++i) pp[i] = a->c[0] * ph[i] + y[i] - b2[i];
+    } else {
+        for (long i = 0; i < N; ++i) pp[i] = a->c[0] * ph[i];
+    }
+    /* Q P(Q^2) psi_h */
+    or_hw(a->d, a->bc, a->U, a->mw, pp, out);
+    for (long i = 0; i < N; ++i) out[i] /= a->lmax;
+    /* + sum_i sign(lam_i) (eta_i^dag psi) eta_i */
+    for (int i = 0; i < a->nev; ++i) {
+        const cplx *e = a->eta + (long)i * N;
+        double sg = a->lam[i] > 0 ? 1.0 : (a->lam[i] < 0 ? -1.0 : 0.0);
+        for (long k = 0; k < N; ++k) out[k] += sg * proj[i] * e[k];
+    }
+    free(ph);
+    free(b1);
+    free(b2);
+    free(y);
+    free(tmp);
+    free(proj);
+}
+
+/* out = sign(H_w(mw)) in (approximated by Eq. 7) */
+void or_sign(const int *d, const double *bc, const cplx *U, double mw, double lmax, double eps,
+             int n, const double *c, int nev, const double *lam, const cplx *eta, const cplx *in,
+             cplx *out)
+{
+    init_gamma();
+    sign_args a = {d, bc, U, mw, lmax, eps, n, c, nev, lam, eta};
+    sign_apply(&a, in, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* overlap operator, Eqs. (3) and (8)                                   */
+/* ------------------------------------------------------------------ */
+/* D psi = psi + gamma_5 sign(H_w(-rho)) psi   (massless, Eq. 3)
+ * D(m) psi = rho D psi + m (1 - D/2) psi     (Eq. 8, lattice spacing a = 1) */
+void or_overlap(const int *d, const double *bc, const cplx *U, double rho, double mass, double lmax,
+                double eps, int n, const double *c, int nev, const double *lam, const cplx *eta,
+                const cplx *in, cplx *out)
+{
+    init_gamma();
+    long V = volume(d), N = 12 * V;
+    sign_args a = {d, bc, U, -rho, lmax, eps, n, c, nev, lam, eta};
+    cplx *s = malloc(sizeof(cplx) * N);
+    sign_apply(&a, in, s);
+    or_gamma5(V, s, s);
+    for (long i = 0; i < N; ++i) {
+        cplx Dpsi = in[i] + s[i];
+        out[i] = rho * Dpsi + mass * (in[i] - 0.5 * Dpsi);
+    }
+    free(s);
+}
+
+/* D(m)^dagger D(m) psi = gamma_5 D(m) gamma_5 D(m) psi (gamma_5-hermiticity of D) */
+static void ddag_d(const sign_args *a, double rho, double mass, const cplx *in, cplx *out, cplx *t)
+{
+    long V = volume(a->d), N = 12 * V;
+    cplx *s = malloc(sizeof(cplx) * N);
+    /* t = D(m) in */
+    sign_apply(a, in, s);
+    or_gamma5(V, s, s);
+    for (long i = 0; i < N; ++i) {
+        cplx Dpsi = in[i] + s[i];
+        t[i] = rho * Dpsi + mass * (in[i] - 0.5 * Dpsi);
+    }
+    /* out = gamma_5 D(m) gamma_5 t */
+    or_gamma5(V, t, t);
+    sign_apply(a, t, s);
+    or_gamma5(V, s, s);
+    for (long i = 0; i < N; ++i) {
+        cplx Dpsi = t[i] + s[i];
+        out[i] = rho * Dpsi + mass * (t[i] - 0.5 * Dpsi);
+    }
+    or_gamma5(V, out, out);
+    free(s);
+}
+
+void or_overlap_normal(const int *d, const double *bc, const cplx *U, double rho, double mass,
+                       double lmax, double eps, int n, const double *c, int nev, const double *lam,
+                       const cplx *eta, const cplx *in, cplx *out)
+{
+    init_gamma();
+    long N = 12 * volume(d);
+    sign_args a = {d, bc, U, -rho, lmax, eps, n, c, nev, lam, eta};
+    cplx *t = malloc(sizeof(cplx) * N);
+    ddag_d(&a, rho, mass, in, out, t);
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* deflated CG on D(m)^dagger D(m), Eq. (9) for the normal equations   */
+/* ------------------------------------------------------------------ */
+/* Solves A x = b, A = D(m)^dag D(m), to ||b - A x|| / ||b|| <= tol.
+ * Deflation with nev2 eigenpairs (mu_i, xi_i) of A: the low part is solved
+ * exactly, x_l = sum_i xi_i (xi_i^dag b) / mu_i (pairs with mu_i <=
+ * zero_tol * mu_max are excluded: exact zero modes, pseudo-inverse), and CG
+ * runs on the orthogonal complement with the residual projected by
+ * P_perp = 1 - sum_i xi_i xi_i^dag after every update.  When the CG
+ * residual meets tol, the true residual b - A x is recomputed; if it does
+ * not meet tol the solve restarts from x with that residual.
+ * Returns the number of CG iterations (negative if max_iter was reached);
+ * *true_res gets the final ||b - A x|| / ||b||. */
+int or_cg(const int *d, const double *bc, const cplx *U, double rho, double mass, double lmax,
+          double eps, int n, const double *c, int nev, const double *lam, const cplx *eta, int nev2,
+          const double *mu, const cplx *xi, double zero_tol, const cplx *b, cplx *x, double tol,
+          int max_iter, double *true_res)
+{
+    init_gamma();
+    long N = 12 * volume(d);
+    sign_args a = {d, bc, U, -rho, lmax, eps, n, c, nev, lam, eta};
+    cplx *r = malloc(sizeof(cplx) * N), *p = malloc(sizeof(cplx) * N);
+    cplx *q = malloc(sizeof(cplx) * N), *t = malloc(sizeof(cplx) * N);
+    double mu_max = 0;
+    for (int i = 0; i < nev2; ++i)
+        if (mu[i] > mu_max) mu_max = mu[i];
+    double bnorm = sqrt(vnorm2(N, b));
+    int iters = 0;
+
+    /* x = x_l (low-mode part, exact) */
+    memset(x, 0, sizeof(cplx) * N);
+    for (int i = 0; i < nev2; ++i) {
+        if (mu[i] <= zero_tol * mu_max) continue;
+        const cplx *e = xi + (long)i * N;
+        cplx pr = vdot(N, e, b) / mu[i];
+        for (long k = 0; k < N; ++k) x[k] += pr * e[k];
+    }
+    double rel = 1.0;
+    for (int cycle = 0; cycle < 20 && iters < max_iter; ++cycle) {
+        /* r = P_perp (b - A x) */
+        ddag_d(&a, rho, mass, x, q, t);
+        for (long k = 0; k < N; ++k) r[k] = b[k] - q[k];
+        rel = sqrt(vnorm2(N, r)) / bnorm;
+        if (rel <= tol) break;
+        for (int i = 0; i < nev2; ++i) {
+            const cplx *e = xi + (long)i * N;
+            cplx pr = vdot(N, e, r);
+            for (long k = 0; k < N; ++k) r[k] -= pr * e[k];
+        }
+        memcpy(p, r, sizeof(cplx) * N);
+        double rr = vnorm2(N, r);
+        while (iters < max_iter) {
+            ddag_d(&a, rho, mass, p, q, t);
+            double pq = creal(vdot(N, p, q));
+            double alpha = rr / pq;
+            for (long k = 0; k < N; ++k) {
+                x[k] += alpha * p[k];
+                r[k] -= alpha * q[k];
+            }
+            for (int i = 0; i < nev2; ++i) {
+                const cplx *e = xi + (long)i * N;
+                cplx pr = vdot(N, e, r);
+                for (long k = 0; k < N; ++k) r[k] -= pr * e[k];
+            }
+            double rr_new = vnorm2(N, r);
+            ++iters;
+            if (sqrt(rr_new) / bnorm <= tol) break;
+            double beta = rr_new / rr;
+            rr = rr_new;
+            for (long k = 0; k < N; ++k) p[k] = r[k] + beta * p[k];
+        }
+    }
+    ddag_d(&a, rho, mass, x, q, t);
+    for (long k = 0; k < N; ++k) r[k] = b[k] - q[k];
+    rel = sqrt(vnorm2(N, r)) / bnorm;
+    *true_res = rel;
+    free(r);
+    free(p);
+    free(q);
+    free(t);
+    return rel <= tol ? iters : -iters;
+}
+
+/* ------------------------------------------------------------------ */
+/* gauge-covariant network layer (the learned preconditioner)           */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart; the layer is defined from the parallel
+ * transporters of Eq. (2) without spin projectors:
+ *   y_c(n) = sum_{c'} sum_{p} W[p][c][c'] (U_p x_{c'})(n),
+ * p = 0: identity; p = 1+2mu: U_mu(n) x(n+mu); p = 2+2mu: U_mu(n-mu)^dag x(n-mu)
+ * (boundary phases applied), W[p][c][c'] a complex 4x4 spin matrix acting on
+ * the spin index.  Fields are [channel][V][4][3]. */
+static void transport(const int *d, const double *bc, const cplx *U, const cplx *x, long n, int p,
+                      cplx out[12])
+{
+    if (p == 0) {
+        memcpy(out, x + n * 12, sizeof(cplx) * 12);
+        return;
+    }
+    int mu = (p - 1) / 2, fwd = ((p - 1) % 2) == 0;
+    double ph;
+    long m = neighbour(d, bc, n, mu, fwd ? +1 : -1, &ph);
+    const cplx *u = fwd ? U + (n * 4 + mu) * 9 : U + (m * 4 + mu) * 9;
+    for (int s = 0; s < 4; ++s)
+        for (int a = 0; a < 3; ++a) {
+            cplx v = 0;
+            for (int b = 0; b < 3; ++b)
+                v += (fwd ? u[3 * a + b] : conj(u[3 * b + a])) * x[m * 12 + 3 * s + b];
+            out[3 * s + a] = ph * v;
+        }
+}
+
+void or_net_layer(const int *d, const double *bc, const cplx *U, int cin, int cout, const cplx *W,
+                  const cplx *x, cplx *y)
+{
+    long V = volume(d);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < V; ++n) {
+        for (int co = 0; co < cout; ++co) {
+            cplx acc[12] = {0};
+            for (int p = 0; p < 9; ++p)
+                for (int ci = 0; ci < cin; ++ci) {
+                    cplx t[12];
+                    transport(d, bc, U, x + (long)ci * V * 12, n, p, t);
+                    const cplx *w = W + (((long)p * cout + co) * cin + ci) * 16;
+                    for (int s = 0; s < 4; ++s)
+                        for (int a = 0; a < 3; ++a) {
+                            cplx v = 0;
+                            for (int s2 = 0; s2 < 4; ++s2) v += w[4 * s + s2] * t[3 * s2 + a];
+                            acc[3 * s + a] += v;
+                        }
+                }
+            memcpy(y + ((long)co * V + n) * 12, acc, sizeof(acc));
+        }
+    }
+}
+
+/* Backward pass of or_net_layer for a real loss L.  gy = dL/dRe(y) + i dL/dIm(y)
+ * [cout][V][12]; returns gx (same convention, [cin][V][12]) and gW [9][cout][cin][16]
+ * with gW = sum_n gy(n) (U_p x(n))^dagger over colour, i.e. dL/dRe W + i dL/dIm W. */
+void or_net_layer_grad(const int *d, const double *bc, const cplx *U, int cin, int cout,
+                       const cplx *W, const cplx *x, const cplx *gy, cplx *gx, cplx *gW)
+{
+    long V = volume(d);
+    memset(gW, 0, sizeof(cplx) * 9 * cout * cin * 16);
+    /* weight gradient: plain accumulation over sites */
+    for (long n = 0; n < V; ++n)
+        for (int p = 0; p < 9; ++p)
+            for (int ci = 0; ci < cin; ++ci) {
+                cplx t[12];
+                transport(d, bc, U, x + (long)ci * V * 12, n, p, t);
+                for (int co = 0; co < cout; ++co) {
+                    const cplx *g = gy + ((long)co * V + n) * 12;
+                    cplx *w = gW + (((long)p * cout + co) * cin + ci) * 16;
+                    for (int s = 0; s < 4; ++s)
+                        for (int s2 = 0; s2 < 4; ++s2) {
+                            cplx v = 0;
+                            for (int a = 0; a < 3; ++a) v += g[3 * s + a] * conj(t[3 * s2 + a]);
+                            w[4 * s + s2] += v;
+                        }
+                }
+            }
+    /* input gradient: gx_{c'}(m) = sum over (n, p) reaching m of T_p^dag W^dag gy_c(n),
+       computed by scattering from every site n */
+    memset(gx, 0, sizeof(cplx) * cin * V * 12);
+    for (long n = 0; n < V; ++n)
+        for (int p = 0; p < 9; ++p) {
+            long m = n;
+            double ph = 1.0;
+            const cplx *u = NULL;
+            int fwd = 0;
+            if (p > 0) {
+                int mu = (p - 1) / 2;
+                fwd = ((p - 1) % 2) == 0;
+                m = neighbour(d, bc, n, mu, fwd ? +1 : -1, &ph);
+                u = fwd ? U + (n * 4 + mu) * 9 : U + (m * 4 + mu) * 9;
+            }
+            for (int ci = 0; ci < cin; ++ci)
+                for (int co = 0; co < cout; ++co) {
+                    const cplx *g = gy + ((long)co * V + n) * 12;
+                    const cplx *w = W + (((long)p * cout + co) * cin + ci) * 16;
+                    cplx h[12]; /* W^dag gy */
+                    for (int s2 = 0; s2 < 4; ++s2)
+                        for (int a = 0; a < 3; ++a) {
+                            cplx v = 0;
+                            for (int s = 0; s < 4; ++s) v += conj(w[4 * s + s2]) * g[3 * s + a];
+                            h[3 * s2 + a] = v;
+                        }
+                    cplx *o = gx + ((long)ci * V + m) * 12;
+                    for (int s = 0; s < 4; ++s)
+                        for (int b = 0; b < 3; ++b) {
+                            cplx v = 0;
+                            if (p == 0)
+                                v = h[3 * s + b];
+                            else
+                                for (int a = 0; a < 3; ++a) /* (link)^dag h: link[a][b] conj */
+                                    v += conj(fwd ? u[3 * a + b] : conj(u[3 * b + a])) * h[3 * s + a];
+                            o[3 * s + b] += ph * v;
+                        }
+                }
+        }
+}
