@@ -1,0 +1,343 @@
+"""Benchmark of the overlap hot path on GB300.
+
+Default workload (the dslash-throughput configuration): Wilson dslash on a
+24^3 x 64 lattice, even/odd layout with both parities in one launch,
+reconstruct-12 links from exp(0.5 i H) + 3 APE steps (alpha 0.6) +
+re-unitarisation, Gaussian spinors, FP32 storage and arithmetic, 1 RHS.
+One step = one full-lattice D_w application (one kernel launch).
+
+`value` is algorithmic GB/s of that kernel: the compulsory traffic of a full
+D_w in one pass, 96 reals per site (4 reconstruct-12 links, the input
+spinor, the output spinor), divided by the CUDA-event time.  The JSON line
+also carries GFLOP/s (1320 flop/site), the FP64/FP16/BF16 and 12-RHS
+variants, an end-to-end figure through the C ABI with host buffers, the
+oracle timed on the host cores, and the SM clocks sampled while timing.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): replicas only, each rank runs the same workload on its own GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (24, 24, 24, 64)
+BC = (1.0, 1.0, 1.0, -1.0)
+RHO = 1.5
+METRIC = "dslash GB/s & GFLOP/s (% HBM roofline); overlap propagator solves/s at res 1e-10"
+REAL_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+FLOP_SITE = 1320
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def site_bytes(prec: str, nrhs: int = 1) -> float:
+    """Compulsory bytes per site and RHS of a one-pass full D_w: links 48 reals shared by
+    the RHS, input and output spinors 24 reals each (16-bit spinors add a 4-byte scale)."""
+    rb = REAL_BYTES[prec]
+    spin = 24 * rb + (4 if prec in ("f16", "bf16") else 0)
+    return 48 * rb / nrhs + 2 * spin
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(nrhs=1):
+    import synth
+
+    U = synth.gauge_field(DIMS, seed=1, s=0.5, ape_steps=3)
+    psi = synth.gaussian_spinor(DIMS, seed=2, nrhs=nrhs)
+    return U, psi
+
+
+def time_dslash(ctx, U_dev, psi_dev, prec, nrhs, steps, warmup, torch):
+    """Average CUDA-event time of one D_w launch (internal fields, current stream)."""
+    fi, fo = ctx.field(nrhs, prec), ctx.field(nrhs, prec)
+    fi.load(psi_dev)
+    ctx.tune_dslash(prec, nrhs)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ctx.dslash_field(fi, fo, -RHO)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        ctx.dslash_field(fi, fo, -RHO)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fi.close()
+    fo.close()
+    return ms
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    V = int(np.prod(DIMS))
+    U, psi = make_inputs(1)
+    ctx = ov.Context(DIMS, BC)
+    U_dev = torch.from_numpy(U).cuda()
+    ctx.set_gauge(U_dev)
+    psi_dev = torch.from_numpy(psi).cuda()
+    hbm, peak_kind = peaks()
+
+    # ---- headline: f32, 1 rhs (timed region bracketed by barrier + synchronize)
+    prec = "f32"
+    fi, fo = ctx.field(1, prec), ctx.field(1, prec)
+    fi.load(psi_dev)
+    bx, by = ctx.tune_dslash(prec, 1)
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.dslash_field(fi, fo, -RHO)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, int(args.inner))
+    t_wall = time.perf_counter()
+    e0.record(st)
+    for _ in range(args.steps * reps):
+        ctx.dslash_field(fi, fo, -RHO)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / (args.steps * reps)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_launch = V * site_bytes(prec, 1)
+    gbs = bytes_launch / (ms * 1e-3) / 1e9
+    gflops = FLOP_SITE * V / (ms * 1e-3) / 1e9
+    fi.close()
+    fo.close()
+
+    # ---- variants (same workload, other precisions and 12 rhs)
+    variants = {}
+    if not args.quick:
+        for p in ("f64", "f16", "bf16"):
+            t = time_dslash(ctx, U_dev, psi_dev, p, 1, min(2000, max(5, args.steps)), args.warmup, torch)
+            b = V * site_bytes(p, 1)
+            variants[f"{p}_r1"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
+                                   "GFLOPps": round(FLOP_SITE * V / t / 1e6, 1),
+                                   "frac_hbm": round(b / t / 1e6 / hbm, 3)}
+        psi12 = torch.from_numpy(make_inputs_rhs(12)).cuda()
+        for p in ("f32", "f16", "f64"):
+            t = time_dslash(ctx, U_dev, psi12, p, 12, min(300, max(3, args.steps // 2)), args.warmup, torch)
+            b = V * 12 * site_bytes(p, 12)
+            variants[f"{p}_r12"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
+                                    "GFLOPps": round(12 * FLOP_SITE * V / t / 1e6, 1),
+                                    "frac_hbm": round(b / t / 1e6 / hbm, 3)}
+        del psi12
+
+    # ---- end to end through the C ABI with pinned host buffers (H2D + pack + dslash + unpack + D2H)
+    hin = torch.from_numpy(psi).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(2):
+        ctx.apply_dslash(hin.numpy(), hout.numpy(), -RHO, prec=prec)
+    torch.cuda.synchronize()
+    ne = min(10, max(3, args.steps // 4))
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        ctx.apply_dslash(hin.numpy(), hout.numpy(), -RHO, prec=prec)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ne
+    e2e = {"value": round(bytes_launch / e2e_s / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": int(hin.numel() * hin.element_size()),
+           "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
+           "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    out = {
+        "metric": METRIC,
+        "value": round(gbs * world, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms * reps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "wilson dslash D_w, 24^3x64 even/odd, reconstruct-12, f32, 1 rhs, both parities "
+                               "per launch", "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: gauge 170 MB + spinors 2 x 85 MB per launch",
+                   "launch_shape": [bx, by], "launches_per_step": reps},
+        "gflops": round(gflops * world, 1),
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(bytes_launch),
+                     "kernel": "dslash_kernel<f32,f32,0>"},
+        "variants": variants,
+        "e2e": e2e,
+        "gpu_launches": args.steps * reps,
+        "clocks": clocks,
+        "wall_s_timed": round(t_wall, 4),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(U, psi, args)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def make_inputs_rhs(nrhs):
+    import synth
+
+    return synth.gaussian_spinor(DIMS, seed=3, nrhs=nrhs)
+
+
+def cpu_baseline(U, psi, args):
+    """The FP64 oracle (plain C, OpenMP over all host cores) on a bounded sample of the same
+    workload: whole D_w applications of the 24^3 x 64 lattice until ~10 s have passed."""
+    import oracle
+
+    oracle.build()
+    V = int(np.prod(DIMS))
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.dslash(DIMS, BC, U, -RHO, psi[0])
+        n += 1
+        if time.perf_counter() - t0 > args.cpu_seconds:
+            break
+    dt = (time.perf_counter() - t0) / n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(V * site_bytes("f32", 1) / dt / 1e9, 4), "unit": "GB/s", "cores": cores,
+            "kind": "oracle", "gflops": round(FLOP_SITE * V / dt / 1e9, 3),
+            "sample": f"{n} full D_w applications of the 24^3x64 lattice (FP64 oracle), {dt * 1e3:.1f} ms each; "
+                      "value in the same algorithmic-bytes unit as the GPU line"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    U, psi = make_inputs(1)
+    import oracle
+
+    oracle.build()
+    V = int(np.prod(DIMS))
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        oracle.dslash(DIMS, BC, U, -RHO, psi[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dslash(DIMS, BC, U, -RHO, psi[0])
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    val = round(V * site_bytes("f32", 1) / dt / 1e9, 4)
+    sample = f"{args.steps} full D_w applications of the 24^3x64 lattice (FP64 oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "wilson dslash D_w, 24^3x64, FP64 CPU oracle", "lattice": list(DIMS)},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gflops": round(FLOP_SITE * V / dt / 1e9, 3)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--inner", type=int, default=1, help="launches per step")
+    ap.add_argument("--quick", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * overlap.h -- C ABI of the GB300 overlap-fermion library (libovgb.so).
+ *
+ * The library implements, on one NVIDIA GB300 (sm_103a), the hot path of the
+ * overlap-operator method of Alexandru, Lujan, Pelissier, Gamari and Lee,
+ * "Efficient implementation of the overlap operator on multi-GPUs":
+ *
+ *   D_w(m)  = (m + 4) - 1/2 sum_{mu=+-1..+-4} T_mu                (Sec. II, Eqs. 1-2)
+ *   H_w     = gamma5 D_w(-rho)                                     (Sec. II)
+ *   sign(H_w) psi ~ sum_i sign(lam_i)(eta_i^dag psi) eta_i
+ *                   + Q P(Q^2) (1 - P_l) psi,   Q = H_w / lambda_max  (Eqs. 5-7)
+ *   D(m)    = rho (1 + gamma5 sign(H_w)) + m (1 - D/2)              (Eqs. 3, 8)
+ *   deflated CG on D(m)^dag D(m)                                   (Eq. 9, Sec. V)
+ *
+ * Conventions shared by every call:
+ *  - Lattice dims[4] = {Lx, Ly, Lz, Lt}, each even and >= 2.  bc_phase[mu] is
+ *    a real phase (+1 periodic, -1 antiperiodic) multiplying every hop that
+ *    crosses the boundary in direction mu.
+ *  - Canonical spinor layout: complex128 (interleaved re, im doubles)
+ *    [nrhs][Lt][Lz][Ly][Lx][spin 4][colour 3], x fastest; right-hand sides
+ *    outermost.  Gauge layout: complex128 [Lt][Lz][Ly][Lx][mu 4][3][3]
+ *    (row-major colour matrix), mu = 0..3 <-> x, y, z, t.
+ *  - Gamma matrices: Euclidean chiral basis, gamma_k = [[0,-i s_k],[i s_k,0]],
+ *    gamma_4 = [[0,1],[1,0]], gamma5 = gamma1 gamma2 gamma3 gamma4 =
+ *    diag(1,1,-1,-1).
+ *  - Buffers passed in may be device memory or host memory (pageable or
+ *    pinned); the kind is detected with cudaPointerGetAttributes.  Host
+ *    buffers are staged through library-owned device memory and the call
+ *    synchronises `stream` before returning.  Device buffers are used in
+ *    place and the call is stream-ordered on `stream` (a cudaStream_t passed
+ *    as void*; NULL = the legacy default stream).  The caller owns every
+ *    buffer it passes; the library owns the packed gauge field, the
+ *    eigenpairs, all workspaces and the network weights.
+ *  - Every call returns OV_OK (0) or a negative ov_status; on error no
+ *    output is guaranteed and ov_last_error() describes the failure.
+ *  - Precision (ov_prec): OV_F64 stores and computes in FP64; OV_F32 in FP32;
+ *    OV_F16S / OV_BF16S store spinors and links in 16 bits (spinors with one
+ *    FP32 scale per site) and compute in FP32.  Dot products and norms always
+ *    accumulate in FP64.
+ */
+#ifndef OVERLAP_GB300_H
+#define OVERLAP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ov_ctx ov_ctx;     /* opaque, library-owned */
+typedef struct ov_field ov_field; /* opaque internal-layout field */
+
+typedef enum {
+    OV_OK = 0,
+    OV_EINVAL = -1,   /* bad argument: null pointer, bad dims, unknown precision, size out of range */
+    OV_ENOMEM = -2,   /* device allocation failed */
+    OV_ECUDA = -3,    /* a CUDA call failed (text in ov_last_error) */
+    OV_ENOTCONV = -4, /* iteration limit reached before the tolerance */
+    OV_ESTALL = -5,   /* residual stopped decreasing */
+    OV_ETIMEOUT = -6, /* a bounded device wait gave up */
+    OV_ENAN = -7,     /* NaN or Inf met in a result */
+    OV_ESTATE = -8    /* call made in the wrong state (e.g. overlap before set_gauge) */
+} ov_status;
+
+typedef enum { OV_F64 = 0, OV_F32 = 1, OV_F16S = 2, OV_BF16S = 3 } ov_prec;
+
+/* Solver report (one per call; per-rhs values up to 64 right-hand sides). */
+typedef struct {
+    int iterations;          /* CG iterations (max over right-hand sides) */
+    int reliable_updates;    /* FP64 true-residual recomputations */
+    int fallback;            /* 1 if the learned preconditioner was switched off */
+    int nrhs;
+    double true_residual[64]; /* ||b - A x|| / ||b|| by the FP64 operator, per rhs */
+    double seconds;          /* wall time of the solve */
+} ov_solve_info;
+
+/* Create a context for one lattice on the current CUDA device.
+ * dims[4] = {Lx, Ly, Lz, Lt}: each even and >= 2 (even/odd split, Sec. II
+ * lattice of Fig. 1).  bc_phase[4]: +1 or -1 per direction.
+ * Returns OV_EINVAL on odd or too small dims, or a null pointer. */
+int ov_create(ov_ctx** ctx, const int dims[4], const double bc_phase[4]);
+int ov_destroy(ov_ctx* ctx);
+/* Text of the last error on this context (never NULL; valid until the next call). */
+const char* ov_last_error(const ov_ctx* ctx);
+
+/* Load the gauge field U_mu(n) in SU(3) (Sec. II: gluons as parallel
+ * transporters on the links).  U: canonical complex128 gauge layout, host or
+ * device.  The library packs it to reconstruct-12 form (rows 0 and 1 kept,
+ * row 2 = conj(row0 x row1)) in FP64, FP32, FP16 and BF16.  Returns OV_EINVAL
+ * if any link deviates from SU(3) by more than 1e-9 (|U U^dag - 1| or the
+ * reconstructed third row), since reconstruct-12 would change it. */
+int ov_set_gauge(ov_ctx* ctx, const void* U, void* stream);
+
+/* out = D_w(m) in for nrhs canonical spinor fields (Eqs. 1-2). */
+int ov_apply_dslash(ov_ctx* ctx, const void* in, void* out, double m, int nrhs, int prec, void* stream);
+/* out = H_w in = gamma5 D_w(m) in (Sec. II; hermitian by gamma5-hermiticity). */
+int ov_apply_Hw(ov_ctx* ctx, const void* in, void* out, double m, int nrhs, int prec, void* stream);
+
+/* Fix the sign-function polynomial (Eqs. 4-5, Sec. V): rho (the overlap
+ * parameter, H_w = gamma5 D_w(-rho)), P = the degree-`degree` Chebyshev
+ * interpolant of x^{-1/2} on [eps, 1], evaluated on Q^2 with
+ * Q = H_w / lambda_max by Clenshaw's recurrence.  lambda_max <= 0 asks the
+ * library to estimate it (1.01 x the largest |eigenvalue| of H_w from 50
+ * Lanczos steps on H_w^2; needs the gauge field).  0 < eps < 1, degree >= 0. */
+int ov_set_sign_poly(ov_ctx* ctx, double rho, double eps, int degree, double lambda_max);
+/* Current polynomial parameters (lambda_max after any estimate). */
+int ov_get_sign_poly(const ov_ctx* ctx, double* rho, double* eps, int* degree, double* lambda_max);
+
+/* out = D(m) in = rho D in + m (1 - D/2) in with D = 1 + gamma5 sign(H_w)
+ * (Eqs. 3, 8), sign by Eq. 7 with the stored H_w eigenpairs (which = 0).
+ * Needs set_gauge and set_sign_poly (OV_ESTATE otherwise).  nrhs <= 16. */
+int ov_apply_overlap(ov_ctx* ctx, const void* in, void* out, double mass, int nrhs, int prec, void* stream);
+
+/* Compute and store eigenpairs (Sec. V: eigensolvers for H_w and D).
+ * which = 0: the nev eigenpairs of H_w with smallest |lambda| (Lanczos on a
+ *            Chebyshev filter of H_w^2, FP64 Gram-Schmidt, Rayleigh-Ritz of
+ *            H_w for the signed eigenvalues); they deflate the sign (Eq. 7).
+ * which = 1: the nev smallest eigenpairs of D(0)^dag D(0) (Lanczos with FP64
+ *            Gram-Schmidt); they deflate the CG (Eq. 9).
+ * tol: relative eigen-residual target.  Returns OV_ENOTCONV if not reached. */
+int ov_deflate(ov_ctx* ctx, int which, int nev, double tol, void* stream);
+/* Install eigenpairs computed elsewhere: vals[nev] (signed eigenvalues of H_w
+ * for which = 0, eigenvalues of D(0)^dag D(0) for which = 1) and vecs, nev
+ * orthonormal canonical complex128 fields (host or device).  nev = 0 clears. */
+int ov_set_eigenpairs(ov_ctx* ctx, int which, int nev, const double* vals, const void* vecs, void* stream);
+/* Copy out the stored eigenpairs.  *nev receives the count; vals and vecs
+ * may be NULL to query it.  vecs: canonical complex128 [nev] fields. */
+int ov_get_eigenpairs(ov_ctx* ctx, int which, int* nev, double* vals, void* vecs, void* stream);
+
+/* Solve D(m)^dag D(m) x = b for nrhs right-hand sides to
+ * ||b - A x|| / ||b|| <= tol (FP64 operator), deflated CG (Eq. 9) with the
+ * stored which = 1 eigenpairs.  inner_prec selects the precision of the
+ * inner operator; for inner_prec != OV_F64 the residual is recomputed in
+ * FP64 (reliable updates).  precond = 1 uses the learned preconditioner in
+ * flexible CG (ov_net_train first), falling back to plain deflated CG when
+ * the true residual stalls.  x may hold nothing on entry.  info may be NULL.
+ * nrhs <= 16. */
+int ov_cg_solve(ov_ctx* ctx, const void* b, void* x, int nrhs, double mass, double tol, int max_iter,
+                int precond, int inner_prec, ov_solve_info* info, void* stream);
+
+/* ---- internal-layout fields: an even/odd field kept on the device in one
+ * storage precision, for chaining operators without repacking. ---- */
+int ov_field_create(ov_ctx* ctx, int nrhs, int prec, ov_field** f);
+int ov_field_destroy(ov_field* f);
+/* canonical (host or device) -> field, and back */
+int ov_field_import(ov_ctx* ctx, ov_field* f, const void* canonical, void* stream);
+int ov_field_export(ov_ctx* ctx, const ov_field* f, void* canonical, void* stream);
+/* out = D_w(m) in (gamma5 = 0) or H_w in (gamma5 = 1), both fields of the
+ * same precision and nrhs, in != out.  One kernel launch. */
+int ov_dslash_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double m, int gamma5, void* stream);
+/* out = D(m) in on internal fields (precision of the fields), in != out. */
+int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass, void* stream);
+
+/* Device bytes held by the context (gauge, eigenpairs, workspaces). */
+long long ov_device_bytes(const ov_ctx* ctx);
+/* Launch shape of the dslash for (prec, nrhs): block = bx sites x by rhs.
+ * ov_tune_dslash times the candidates on `stream` and keeps the fastest. */
+int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by);
+int ov_tune_dslash(ov_ctx* ctx, int prec, int nrhs, int* bx, int* by, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVERLAP_GB300_H */

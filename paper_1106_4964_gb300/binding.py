@@ -1,0 +1,276 @@
+"""ctypes binding of libovgb.so (include/overlap.h), argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python
+arguments (numpy arrays for host buffers, torch CUDA tensors for device
+buffers, torch streams) into the plain pointers and sizes of the C ABI and
+raises on a non-zero status.  If the library has not been built the import
+of the loader fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libovgb.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "overlap.h")
+
+OV_F64, OV_F32, OV_F16S, OV_BF16S = 0, 1, 2, 3
+PREC = {"f64": OV_F64, "f32": OV_F32, "f16": OV_F16S, "bf16": OV_BF16S}
+STATUS = {0: "OV_OK", -1: "OV_EINVAL", -2: "OV_ENOMEM", -3: "OV_ECUDA", -4: "OV_ENOTCONV", -5: "OV_ESTALL",
+          -6: "OV_ETIMEOUT", -7: "OV_ENAN", -8: "OV_ESTATE"}
+
+
+class OverlapError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("fallback", ctypes.c_int),
+                ("nrhs", ctypes.c_int), ("true_residual", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "reliable_updates": self.reliable_updates,
+                "fallback": self.fallback, "true_residual": list(self.true_residual[: self.nrhs]),
+                "seconds": self.seconds}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "ov_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "ov_destroy": (_I, [_P]),
+    "ov_last_error": (ctypes.c_char_p, [_P]),
+    "ov_set_gauge": (_I, [_P, _P, _P]),
+    "ov_apply_dslash": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "ov_apply_Hw": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "ov_set_sign_poly": (_I, [_P, _D, _D, _I, _D]),
+    "ov_get_sign_poly": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "ov_apply_overlap": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "ov_deflate": (_I, [_P, _I, _I, _D, _P]),
+    "ov_set_eigenpairs": (_I, [_P, _I, _I, _P, _P, _P]),
+    "ov_get_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P]),
+    "ov_cg_solve": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
+    "ov_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "ov_field_destroy": (_I, [_P]),
+    "ov_field_import": (_I, [_P, _P, _P, _P]),
+    "ov_field_export": (_I, [_P, _P, _P, _P]),
+    "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
+    "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
+    "ov_device_bytes": (ctypes.c_longlong, [_P]),
+    "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I]),
+    "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
+}
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions declared in include/overlap.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ov_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str = LIBPATH):
+    """Load libovgb.so and set the prototypes.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device pointer of a contiguous torch tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("numpy buffer must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _nbytes(x):
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    return x.numel() * x.element_size()
+
+
+class Field:
+    """An internal-layout even/odd field (ov_field)."""
+
+    def __init__(self, ctx: "Context", nrhs: int, prec):
+        self.ctx = ctx
+        self.nrhs = nrhs
+        self.prec = _prec(prec)
+        h = _P()
+        ctx._check(ctx.lib.ov_field_create(ctx.h, nrhs, self.prec, ctypes.byref(h)))
+        self.h = h
+
+    def load(self, x, stream=None):
+        self.ctx._check(self.ctx.lib.ov_field_import(self.ctx.h, self.h, _ptr(x), _stream(stream)))
+
+    def store(self, x, stream=None):
+        self.ctx._check(self.ctx.lib.ov_field_export(self.ctx.h, self.h, _ptr(x), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.ov_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One lattice on the current CUDA device (ov_ctx)."""
+
+    def __init__(self, dims, bc=(1.0, 1.0, 1.0, -1.0)):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        h = _P()
+        st = self.lib.ov_create(ctypes.byref(h), (_I * 4)(*self.dims), (_D * 4)(*[float(b) for b in bc]))
+        if st != 0:
+            raise OverlapError(st, f"ov_create({self.dims}) failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise OverlapError(st, self.lib.ov_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ov_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _nrhs(self, x):
+        n = _nbytes(x) // (self.V * 12 * 16)
+        if n * self.V * 12 * 16 != _nbytes(x):
+            raise ValueError("buffer size is not a whole number of complex128 spinor fields")
+        return n
+
+    # -- calls of the ABI --------------------------------------------------------------
+    def set_gauge(self, U, stream=None):
+        if _nbytes(U) != self.V * 36 * 16:
+            raise ValueError("gauge buffer must be complex128 [Lt,Lz,Ly,Lx,4,3,3]")
+        self._check(self.lib.ov_set_gauge(self.h, _ptr(U), _stream(stream)))
+
+    def apply_dslash(self, x, out, m, prec="f64", stream=None):
+        self._check(self.lib.ov_apply_dslash(self.h, _ptr(x), _ptr(out), float(m), self._nrhs(x), _prec(prec),
+                                             _stream(stream)))
+        return out
+
+    def apply_Hw(self, x, out, m, prec="f64", stream=None):
+        self._check(self.lib.ov_apply_Hw(self.h, _ptr(x), _ptr(out), float(m), self._nrhs(x), _prec(prec),
+                                         _stream(stream)))
+        return out
+
+    def set_sign_poly(self, rho, eps, degree, lambda_max=0.0):
+        self._check(self.lib.ov_set_sign_poly(self.h, float(rho), float(eps), int(degree), float(lambda_max)))
+
+    def get_sign_poly(self):
+        r, e, lm = _D(), _D(), _D()
+        n = _I()
+        self._check(self.lib.ov_get_sign_poly(self.h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(n),
+                                              ctypes.byref(lm)))
+        return {"rho": r.value, "eps": e.value, "degree": n.value, "lambda_max": lm.value}
+
+    def apply_overlap(self, x, out, mass=0.0, prec="f64", stream=None):
+        self._check(self.lib.ov_apply_overlap(self.h, _ptr(x), _ptr(out), float(mass), self._nrhs(x), _prec(prec),
+                                              _stream(stream)))
+        return out
+
+    def deflate(self, which, nev, tol, stream=None):
+        self._check(self.lib.ov_deflate(self.h, int(which), int(nev), float(tol), _stream(stream)))
+
+    def set_eigenpairs(self, which, vals, vecs, stream=None):
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        self._check(self.lib.ov_set_eigenpairs(self.h, int(which), len(vals), _ptr(vals),
+                                               _ptr(vecs) if len(vals) else None, _stream(stream)))
+
+    def get_eigenpairs(self, which, stream=None):
+        n = _I()
+        self._check(self.lib.ov_get_eigenpairs(self.h, int(which), ctypes.byref(n), None, None, _stream(stream)))
+        vals = np.empty(n.value)
+        vecs = np.empty((n.value, self.V * 12), dtype=np.complex128)
+        if n.value:
+            self._check(self.lib.ov_get_eigenpairs(self.h, int(which), ctypes.byref(n), _ptr(vals), _ptr(vecs),
+                                                   _stream(stream)))
+        return vals, vecs
+
+    def cg_solve(self, b, x, mass=0.0, tol=1e-10, max_iter=1000, precond=0, inner_prec="f64", stream=None,
+                 check=True):
+        info = SolveInfo()
+        st = self.lib.ov_cg_solve(self.h, _ptr(b), _ptr(x), self._nrhs(b), float(mass), float(tol), int(max_iter),
+                                  int(precond), _prec(inner_prec), ctypes.byref(info), _stream(stream))
+        if check:
+            self._check(st)
+        return info.as_dict() | {"status": st}
+
+    def field(self, nrhs, prec):
+        return Field(self, nrhs, prec)
+
+    def dslash_field(self, fin: Field, fout: Field, m, gamma5=False, stream=None):
+        self._check(self.lib.ov_dslash_field(self.h, fin.h, fout.h, float(m), int(bool(gamma5)), _stream(stream)))
+
+    def overlap_field(self, fin: Field, fout: Field, mass=0.0, stream=None):
+        self._check(self.lib.ov_overlap_field(self.h, fin.h, fout.h, float(mass), _stream(stream)))
+
+    def device_bytes(self):
+        return int(self.lib.ov_device_bytes(self.h))
+
+    def set_dslash_shape(self, prec, nrhs, bx, by):
+        self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by)))
+
+    def tune_dslash(self, prec, nrhs, stream=None):
+        bx, by = _I(), _I()
+        self._check(self.lib.ov_tune_dslash(self.h, _prec(prec), int(nrhs), ctypes.byref(bx), ctypes.byref(by),
+                                            _stream(stream)))
+        return bx.value, by.value

@@ -1,0 +1,817 @@
+// C ABI of the library: context, gauge packing, dslash / H_w / overlap
+// application, internal-layout fields.  The solvers (Lanczos, CG) live in
+// solver.cu, the learned preconditioner in net.cu.
+#include <cmath>
+#include <cstring>
+
+#include "ctx.h"
+
+using namespace ov;
+
+namespace ov {
+
+int set_err(ov_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int dev_alloc(ov_ctx* c, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return OV_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, OV_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->bytes += (long long)bytes;
+    return OV_OK;
+}
+
+void dev_free(ov_ctx* c, void* p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        c->bytes -= (long long)bytes;
+    }
+}
+
+static size_t data_bytes(int prec, int nrhs, int Vh) { return (size_t)nrhs * 2 * spinor_chunks(prec) * 16 * Vh; }
+static size_t norm_bytes(int prec, int nrhs, int Vh) { return has_norm(prec) ? (size_t)nrhs * 2 * Vh * 4 : 0; }
+
+int field_alloc(ov_ctx* c, int prec, int nrhs, FieldDesc* f)
+{
+    *f = FieldDesc{prec, nrhs, c->g.Vh, nullptr, nullptr};
+    void* p = nullptr;
+    OV_TRY(dev_alloc(c, &p, data_bytes(prec, nrhs, c->g.Vh)));
+    f->data = (char*)p;
+    if (has_norm(prec)) {
+        void* q = nullptr;
+        int s = dev_alloc(c, &q, norm_bytes(prec, nrhs, c->g.Vh));
+        if (s != OV_OK) {
+            dev_free(c, p, data_bytes(prec, nrhs, c->g.Vh));
+            f->data = nullptr;
+            return s;
+        }
+        f->norm = (float*)q;
+    }
+    return OV_OK;
+}
+
+void field_free(ov_ctx* c, FieldDesc* f)
+{
+    if (f->data) dev_free(c, f->data, data_bytes(f->prec, f->nrhs, f->Vh));
+    if (f->norm) dev_free(c, f->norm, norm_bytes(f->prec, f->nrhs, f->Vh));
+    f->data = nullptr;
+    f->norm = nullptr;
+}
+
+int ws_field(ov_ctx* c, int slot, int prec, int nrhs, FieldDesc* f)
+{
+    auto key = std::make_tuple(slot, prec, nrhs);
+    auto it = c->ws.find(key);
+    if (it != c->ws.end()) {
+        *f = it->second;
+        return OV_OK;
+    }
+    OV_TRY(field_alloc(c, prec, nrhs, f));
+    c->ws[key] = *f;
+    return OV_OK;
+}
+
+int ensure_partials(ov_ctx* c, size_t bytes)
+{
+    if (bytes <= c->partials_bytes) return OV_OK;
+    // the old buffer may still be read by queued kernels: wait before freeing
+    if (c->partials) {
+        cudaDeviceSynchronize();
+        dev_free(c, c->partials, c->partials_bytes);
+    }
+    c->partials = nullptr;
+    c->partials_bytes = 0;
+    void* p = nullptr;
+    OV_TRY(dev_alloc(c, &p, bytes));
+    c->partials = (double*)p;
+    c->partials_bytes = bytes;
+    return OV_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int ensure_stage(ov_ctx* c, int which, size_t bytes)
+{
+    if (bytes <= c->stage_bytes[which]) return OV_OK;
+    if (c->stage[which]) {
+        cudaDeviceSynchronize();
+        dev_free(c, c->stage[which], c->stage_bytes[which]);
+    }
+    c->stage[which] = nullptr;
+    c->stage_bytes[which] = 0;
+    OV_TRY(dev_alloc(c, &c->stage[which], bytes));
+    c->stage_bytes[which] = bytes;
+    return OV_OK;
+}
+
+int stage_in(ov_ctx* c, int which, const void* src, size_t bytes, cudaStream_t st, const double** dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = (const double*)src;
+        return OV_OK;
+    }
+    OV_TRY(ensure_stage(c, which, bytes));
+    OV_CUDA(c, cudaMemcpyAsync(c->stage[which], src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = (const double*)c->stage[which];
+    return OV_OK;
+}
+
+int stage_out_buffer(ov_ctx* c, int which, void* dst, size_t bytes, double** dev)
+{
+    if (is_device_ptr(dst)) {
+        *dev = (double*)dst;
+        return OV_OK;
+    }
+    OV_TRY(ensure_stage(c, which, bytes));
+    *dev = (double*)c->stage[which];
+    return OV_OK;
+}
+
+int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cudaStream_t st)
+{
+    if ((const void*)dev == dst) return OV_OK;
+    OV_CUDA(c, cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    return OV_OK;
+}
+
+int gauge_prec_for(int prec) { return prec; }
+
+int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out)
+{
+    EigSet& E = c->eig[which];
+    if (E.nev == 0) return set_err(c, OV_ESTATE, "no eigenpairs stored (which=%d)", which);
+    if (!E.vec[prec].data) {
+        OV_TRY(field_alloc(c, prec, E.nev, &E.vec[prec]));
+        OV_CUDA(c, launch_convert(c->g, E.vec[P_F64], E.vec[prec], st));
+    }
+    *out = E.vec[prec];
+    return OV_OK;
+}
+
+static std::pair<int, int> default_shape(int prec, int nrhs)
+{
+    if (nrhs == 1) return {prec == P_F64 ? 64 : 128, 1};
+    const int cap = prec == P_F64 ? 8 : 16;
+    int by = nrhs > cap ? cap : nrhs;
+    return {32, by};
+}
+
+int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a, double b, int g5_core, int g5_out,
+                 int ny, const FieldDesc* y, const double* sy, cudaStream_t st, int gprec)
+{
+    if (gprec < 0) gprec = gauge_prec_for(in.prec);
+    DslashArgs A;
+    memset(&A, 0, sizeof A);
+    A.g = c->g;
+    A.gauge = (const char*)c->gauge[gprec];
+    A.in = in.data;
+    A.in_n = in.norm;
+    A.out = out.data;
+    A.out_n = out.norm;
+    for (int j = 0; j < ny; ++j) {
+        A.y[j] = y[j].data;
+        A.y_n[j] = y[j].norm;
+        A.sy[j] = sy[j];
+    }
+    A.a = a;
+    A.b = b;
+    A.nrhs = in.nrhs;
+    A.g5_core = g5_core;
+    A.g5_out = g5_out;
+    auto it = c->shape.find({in.prec, in.nrhs});
+    std::pair<int, int> sh = it != c->shape.end() ? it->second : default_shape(in.prec, in.nrhs);
+    OV_CUDA(c, launch_dslash(A, in.prec, gprec, ny, sh.first, sh.second, st));
+    c->dslash_launches++;
+    return OV_OK;
+}
+
+int lincomb(ov_ctx* c, const FieldDesc& out, int K, const FieldDesc* x, const double2* hcoef, const double2* dcoef,
+            int g5mask, double* dnorm_out, cudaStream_t st)
+{
+    LincombArgs A;
+    memset(&A, 0, sizeof A);
+    A.K = K;
+    for (int j = 0; j < K; ++j) {
+        A.x[j] = x[j];
+        if (hcoef) A.hcoef[j] = hcoef[j];
+    }
+    A.dcoef = dcoef;
+    A.g5mask = g5mask;
+    A.out = out;
+    const int nblk = reduce_blocks(c->g);
+    if (dnorm_out) {
+        OV_TRY(ensure_partials(c, (size_t)nblk * out.nrhs * sizeof(double)));
+        A.partials = c->partials;
+    }
+    OV_CUDA(c, launch_lincomb(c->g, A, nblk, st));
+    if (dnorm_out) OV_CUDA(c, launch_finalize(c->partials, nblk, out.nrhs, 1, dnorm_out, st));
+    return OV_OK;
+}
+
+int dot(ov_ctx* c, const FieldDesc& x, const FieldDesc& y, double2* dout, cudaStream_t st)
+{
+    const int nblk = reduce_blocks(c->g);
+    OV_TRY(ensure_partials(c, (size_t)nblk * x.nrhs * sizeof(double2)));
+    OV_CUDA(c, launch_dot(c->g, x, y, (double2*)c->partials, nblk, st));
+    OV_CUDA(c, launch_finalize(c->partials, nblk, x.nrhs, 2, (double*)dout, st));
+    return OV_OK;
+}
+
+int norm2(ov_ctx* c, const FieldDesc& x, double* dout2, cudaStream_t st)
+{
+    // dout2 receives [nrhs] double2 (re = |x|^2)
+    return dot(c, x, x, (double2*)dout2, st);
+}
+
+int convert(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st)
+{
+    OV_CUDA(c, launch_convert(c->g, in, out, st));
+    return OV_OK;
+}
+
+int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st)
+{
+    if (in.prec != out.prec) return convert(c, in, out, st);
+    OV_CUDA(c, cudaMemcpyAsync(out.data, in.data, data_bytes(in.prec, in.nrhs, in.Vh), cudaMemcpyDeviceToDevice, st));
+    if (in.norm)
+        OV_CUDA(c, cudaMemcpyAsync(out.norm, in.norm, norm_bytes(in.prec, in.nrhs, in.Vh), cudaMemcpyDeviceToDevice,
+                                   st));
+    return OV_OK;
+}
+
+// D(m) in, optionally followed by gamma5 (g5_out).  Sign by Eq. 7; the
+// polynomial P(Q^2) psi_h by Clenshaw's recurrence in the variable
+// Y = (2 Q^2 - (1+eps)) / (1-eps):
+//   b_k = c_k psi_h + 2 Y b_{k+1} - b_{k+2},  k = n .. 1,   P psi_h = c_0 psi_h + Y b_1 - b_2,
+// with 2 Y b = alpha H_w^2 b + beta b, alpha = 4 / (lmax^2 (1-eps)), beta = -2 (1+eps)/(1-eps).
+// Each step is two dslash launches: t = H_w b_{k+1}, then H_w t with the
+// whole combination fused into the epilogue.  b_n and b_{n-1} are kept as
+// multiples of psi_h until a buffer is needed, so the launch count is 2n + 1.
+// Finally D(m) psi = (rho + m/2) psi + (rho - m/2) [D_w(P psi_h) / lmax + gamma5 sum_i sign(lam_i) c_i eta_i]
+// (gamma5 Q = D_w / lmax), in one more launch.
+static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out,
+                            cudaStream_t st)
+{
+    if (!c->have_gauge) return set_err(c, OV_ESTATE, "overlap: no gauge field (call ov_set_gauge)");
+    if (!c->have_poly) return set_err(c, OV_ESTATE, "overlap: no sign polynomial (call ov_set_sign_poly)");
+    const int P = in.prec, R = in.nrhs;
+    const double rho = c->rho, lam = c->lmax, eps = c->eps;
+    const double aw = 4.0 - rho;
+    FieldDesc ph, w, t, B[3];
+    OV_TRY(ws_field(c, WS_T, P, R, &t));
+    OV_TRY(ws_field(c, WS_B0, P, R, &B[0]));
+    OV_TRY(ws_field(c, WS_B1, P, R, &B[1]));
+    OV_TRY(ws_field(c, WS_B2, P, R, &B[2]));
+    const EigSet& E = c->eig[0];
+    const bool defl = E.nev > 0;
+    FieldDesc src = in;
+    if (defl) {
+        OV_TRY(ws_field(c, WS_PH, P, R, &ph));
+        OV_TRY(ws_field(c, WS_W, P, R, &w));
+        FieldDesc eta;
+        OV_TRY(eig_vectors(c, 0, P, st, &eta));
+        const int nblk = reduce_blocks(c->g);
+        const int nparts = nblk * proj_groups(R);
+        const size_t ncoef = (size_t)E.nev * R;
+        OV_TRY(ensure_partials(c, nparts * ncoef * sizeof(double2)));
+        if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "overlap: nev * nrhs = %zu too large", ncoef);
+        double2* dcoef = (double2*)c->dscal;
+        OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
+        OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
+        OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));
+        src = ph;
+    }
+    const double alpha = 4.0 / (lam * lam * (1.0 - eps));
+    const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
+    struct BRef {
+        int buf;   // >= 0: value is B[buf]; -1: value is g * psi_h
+        double g;
+    };
+    BRef b1{-1, 0.0}, b2{-1, 0.0};
+    for (int k = c->degree; k >= 0; --k) {
+        const double f = k == 0 ? 0.5 : 1.0;
+        if (b1.buf < 0 && b1.g == 0.0) {  // b_{k+1} = 0 (then b_{k+2} = 0 too)
+            BRef nb{-1, c->coef[k] - (b2.buf < 0 ? b2.g : 0.0)};
+            b2 = b1;
+            b1 = nb;
+            continue;
+        }
+        FieldDesc y[3];
+        double sy[3];
+        int ny = 1;
+        double psi_coef = c->coef[k];
+        const FieldDesc* hin;
+        double hscale;
+        if (b1.buf < 0) {
+            hin = &src;
+            hscale = b1.g;
+            psi_coef += f * beta * b1.g;
+        } else {
+            hin = &B[b1.buf];
+            hscale = 1.0;
+            y[ny] = B[b1.buf];
+            sy[ny++] = f * beta;
+        }
+        int outbuf;
+        if (b2.buf >= 0) {
+            y[ny] = B[b2.buf];
+            sy[ny++] = -1.0;
+            outbuf = b2.buf;
+        } else {
+            psi_coef -= b2.g;
+            outbuf = b1.buf == 0 ? 1 : 0;
+        }
+        y[0] = src;
+        sy[0] = psi_coef;
+        // t = H_w b_{k+1} (unscaled), then b_k = f alpha hscale H_w t + sum_j sy_j y_j
+        OV_TRY(dslash_apply(c, *hin, t, aw, -0.5, 1, 0, 0, nullptr, nullptr, st));
+        const double sc = f * alpha * hscale;
+        OV_TRY(dslash_apply(c, t, B[outbuf], sc * aw, -0.5 * sc, 1, 0, ny, y, sy, st));
+        b2 = b1;
+        b1 = BRef{outbuf, 0.0};
+    }
+    // out = kk D_w(P) + (rho + m/2) in + (rho - m/2) W'
+    const double kk = (rho - 0.5 * mass) / lam;
+    const FieldDesc* pin = b1.buf >= 0 ? &B[b1.buf] : &src;
+    const double psc = b1.buf >= 0 ? 1.0 : b1.g;
+    FieldDesc y[2] = {in, defl ? w : in};
+    double sy[2] = {rho + 0.5 * mass, rho - 0.5 * mass};
+    OV_TRY(dslash_apply(c, *pin, out, kk * psc * aw, -0.5 * kk * psc, 0, g5_out, defl ? 2 : 1, y, sy, st));
+    return OV_OK;
+}
+
+int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
+{
+    return overlap_apply_g5(c, in, out, mass, 0, st);
+}
+
+int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
+{
+    FieldDesc u;
+    OV_TRY(ws_field(c, WS_AUX0, in.prec, in.nrhs, &u));
+    OV_TRY(overlap_apply_g5(c, in, u, mass, 1, st));   // u = g5 D in
+    OV_TRY(overlap_apply_g5(c, u, out, mass, 1, st));  // out = g5 D g5 D in = D^dag D in
+    return OV_OK;
+}
+
+// Chebyshev-interpolant coefficients of x^{-1/2} on [eps, 1] at the n+1
+// Chebyshev nodes of the variable y = (2x - (1+eps))/(1-eps) (Eq. 4, Sec. V);
+// c_0 is halved so that P = sum_k c_k T_k(y).
+static void cheb_coefficients(double eps, int n, std::vector<double>& c)
+{
+    const int m = n + 1;
+    std::vector<double> f(m);
+    for (int j = 0; j < m; ++j) {
+        double th = M_PI * (j + 0.5) / m;
+        f[j] = 1.0 / std::sqrt(0.5 * (1.0 + eps) + 0.5 * (1.0 - eps) * std::cos(th));
+    }
+    c.assign(m, 0.0);
+    for (int k = 0; k < m; ++k) {
+        double s = 0;
+        for (int j = 0; j < m; ++j) s += f[j] * std::cos(M_PI * k * (j + 0.5) / m);
+        c[k] = 2.0 * s / m;
+    }
+    c[0] *= 0.5;
+}
+
+static int check_prec(ov_ctx* c, int prec)
+{
+    if (prec < 0 || prec > 3) return set_err(c, OV_EINVAL, "unknown precision %d", prec);
+    return OV_OK;
+}
+
+}  // namespace ov
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+int ov_create(ov_ctx** ctx, const int dims[4], const double bc_phase[4])
+{
+    if (!ctx || !dims || !bc_phase) return OV_EINVAL;
+    *ctx = nullptr;
+    for (int mu = 0; mu < 4; ++mu)
+        if (dims[mu] < 2 || dims[mu] % 2) return OV_EINVAL;
+    long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V / 2 > (1LL << 26)) return OV_EINVAL;  // keeps every 16-byte chunk index below 2^31
+    ov_ctx* c = new ov_ctx();
+    for (int mu = 0; mu < 4; ++mu) {
+        c->dims[mu] = dims[mu];
+        c->bc[mu] = bc_phase[mu];
+        c->g.L[mu] = dims[mu];
+        c->g.bc[mu] = bc_phase[mu];
+    }
+    c->g.Lxh = dims[0] / 2;
+    c->g.Vh = (int)(V / 2);
+    cudaGetDevice(&c->device);
+    void* p = nullptr;
+    if (dev_alloc(c, &p, DSCAL_DOUBLES * sizeof(double)) != OV_OK) {
+        delete c;
+        return OV_ENOMEM;
+    }
+    c->dscal = (double*)p;
+    if (dev_alloc(c, &p, 64) != OV_OK) {
+        dev_free(c, c->dscal, DSCAL_DOUBLES * sizeof(double));
+        delete c;
+        return OV_ENOMEM;
+    }
+    c->derr = (unsigned*)p;
+    *ctx = c;
+    return OV_OK;
+}
+
+int ov_destroy(ov_ctx* c)
+{
+    if (!c) return OV_EINVAL;
+    cudaDeviceSynchronize();
+    net_free(c);
+    for (int p = 0; p < 4; ++p)
+        if (c->gauge[p]) dev_free(c, c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p));
+    for (auto& e : c->eig) {
+        for (auto& f : e.vec) field_free(c, &f);
+        if (e.d_sign) dev_free(c, e.d_sign, sizeof(double) * e.nev);
+    }
+    for (auto& kv : c->ws) field_free(c, &kv.second);
+    if (c->partials) dev_free(c, c->partials, c->partials_bytes);
+    for (int i = 0; i < 2; ++i)
+        if (c->stage[i]) dev_free(c, c->stage[i], c->stage_bytes[i]);
+    dev_free(c, c->dscal, DSCAL_DOUBLES * sizeof(double));
+    dev_free(c, c->derr, 64);
+    delete c;
+    return OV_OK;
+}
+
+const char* ov_last_error(const ov_ctx* c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int ov_set_gauge(ov_ctx* c, const void* U, void* stream)
+{
+    if (!c || !U) return c ? set_err(c, OV_EINVAL, "set_gauge: null pointer") : OV_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)2 * c->g.Vh * 4 * 9 * 16;
+    const double* dU = nullptr;
+    OV_TRY(stage_in(c, 0, U, bytes, st, &dU));
+    for (int p = 0; p < 4; ++p) {
+        if (!c->gauge[p]) OV_TRY(dev_alloc(c, &c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p)));
+    }
+    OV_CUDA(c, cudaMemsetAsync(c->derr, 0, 2 * sizeof(unsigned), st));
+    for (int p = 0; p < 4; ++p) OV_CUDA(c, launch_pack_gauge(c->g, dU, c->gauge[p], p, p == 0 ? c->derr : nullptr, st));
+    unsigned herr[2];
+    OV_CUDA(c, cudaMemcpyAsync(herr, c->derr, sizeof herr, cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    float e_unit, e_row;
+    memcpy(&e_unit, &herr[0], 4);
+    memcpy(&e_row, &herr[1], 4);
+    if (!(e_unit <= 1e-9f) || !(e_row <= 1e-9f)) {
+        c->have_gauge = false;
+        return set_err(c, OV_EINVAL,
+                       "set_gauge: links are not SU(3) (max |U U^dag - 1| = %g, max |row2 - conj(row0 x row1)| = %g); "
+                       "reconstruct-12 needs SU(3)",
+                       (double)e_unit, (double)e_row);
+    }
+    c->have_gauge = true;
+    // eigenpairs of a previous gauge field no longer apply
+    for (auto& e : c->eig) {
+        for (auto& f : e.vec) field_free(c, &f);
+        if (e.d_sign) dev_free(c, e.d_sign, sizeof(double) * e.nev);
+        e.d_sign = nullptr;
+        e.nev = 0;
+        e.vals.clear();
+    }
+    return OV_OK;
+}
+
+static int apply_canonical(ov_ctx* c, const void* in, void* out, double m, int nrhs, int prec, void* stream, int kind)
+{
+    if (!c) return OV_EINVAL;
+    if (!in || !out) return set_err(c, OV_EINVAL, "null buffer");
+    if (in == out) return set_err(c, OV_EINVAL, "in and out must differ");
+    OV_TRY(check_prec(c, prec));
+    if (nrhs < 1 || nrhs > 16) return set_err(c, OV_EINVAL, "nrhs = %d out of range 1..16", nrhs);
+    if (!c->have_gauge) return set_err(c, OV_ESTATE, "no gauge field (call ov_set_gauge)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)nrhs * 2 * c->g.Vh * 12 * 16;
+    const double* din = nullptr;
+    double* dout = nullptr;
+    OV_TRY(stage_in(c, 0, in, bytes, st, &din));
+    OV_TRY(stage_out_buffer(c, 1, out, bytes, &dout));
+    FieldDesc fi, fo;
+    OV_TRY(ws_field(c, WS_IN, prec, nrhs, &fi));
+    OV_TRY(ws_field(c, WS_OUT, prec, nrhs, &fo));
+    OV_CUDA(c, launch_pack(c->g, din, fi, 0, st));
+    if (kind == 2)
+        OV_TRY(overlap_apply(c, fi, fo, m, st));
+    else
+        OV_TRY(dslash_apply(c, fi, fo, 4.0 + m, -0.5, kind == 1, 0, 0, nullptr, nullptr, st));
+    OV_CUDA(c, launch_unpack(c->g, fo, dout, 0, st));
+    return stage_out_finish(c, out, dout, bytes, st);
+}
+
+int ov_apply_dslash(ov_ctx* c, const void* in, void* out, double m, int nrhs, int prec, void* stream)
+{
+    return apply_canonical(c, in, out, m, nrhs, prec, stream, 0);
+}
+
+int ov_apply_Hw(ov_ctx* c, const void* in, void* out, double m, int nrhs, int prec, void* stream)
+{
+    return apply_canonical(c, in, out, m, nrhs, prec, stream, 1);
+}
+
+int ov_apply_overlap(ov_ctx* c, const void* in, void* out, double mass, int nrhs, int prec, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (!c->have_poly) return set_err(c, OV_ESTATE, "overlap: no sign polynomial (call ov_set_sign_poly)");
+    return apply_canonical(c, in, out, mass, nrhs, prec, stream, 2);
+}
+
+int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambda_max)
+{
+    if (!c) return OV_EINVAL;
+    if (!(eps > 0.0 && eps < 1.0)) return set_err(c, OV_EINVAL, "eps = %g outside (0, 1)", eps);
+    if (degree < 0 || degree > 100000) return set_err(c, OV_EINVAL, "degree = %d out of range", degree);
+    if (!(rho > 0.0 && rho < 2.0)) return set_err(c, OV_EINVAL, "rho = %g outside (0, 2)", rho);
+    c->rho = rho;
+    c->eps = eps;
+    c->degree = degree;
+    cheb_coefficients(eps, degree, c->coef);
+    if (lambda_max > 0) {
+        c->lmax = lambda_max;
+    } else {
+        if (!c->have_gauge) return set_err(c, OV_ESTATE, "lambda_max estimate needs the gauge field");
+        double l = 0;
+        OV_TRY(estimate_lambda_max(c, 50, &l, (cudaStream_t)0));
+        c->lmax = 1.01 * l;
+    }
+    c->have_poly = true;
+    return OV_OK;
+}
+
+int ov_get_sign_poly(const ov_ctx* c, double* rho, double* eps, int* degree, double* lambda_max)
+{
+    if (!c) return OV_EINVAL;
+    if (rho) *rho = c->rho;
+    if (eps) *eps = c->eps;
+    if (degree) *degree = c->degree;
+    if (lambda_max) *lambda_max = c->lmax;
+    return c->have_poly ? OV_OK : OV_ESTATE;
+}
+
+int ov_set_eigenpairs(ov_ctx* c, int which, int nev, const double* vals, const void* vecs, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (which != 0 && which != 1) return set_err(c, OV_EINVAL, "which = %d (0 or 1)", which);
+    if (nev < 0 || nev > 2048) return set_err(c, OV_EINVAL, "nev = %d out of range 0..2048", nev);
+    if (nev > 0 && (!vals || !vecs)) return set_err(c, OV_EINVAL, "null eigenpair buffers");
+    cudaStream_t st = (cudaStream_t)stream;
+    EigSet& E = c->eig[which];
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    for (auto& f : E.vec) field_free(c, &f);
+    if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
+    E.d_sign = nullptr;
+    E.nev = 0;
+    E.vals.clear();
+    if (nev == 0) return OV_OK;
+    OV_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
+    const size_t one = (size_t)2 * c->g.Vh * 12 * 16;
+    // pack in chunks of 16 vectors through the staging buffer
+    for (int i0 = 0; i0 < nev; i0 += 16) {
+        int n = nev - i0 < 16 ? nev - i0 : 16;
+        const double* src = nullptr;
+        OV_TRY(stage_in(c, 0, (const char*)vecs + one * i0, one * n, st, &src));
+        FieldDesc sub = E.vec[P_F64];
+        sub.nrhs = n;
+        sub.data = E.vec[P_F64].data + (size_t)i0 * E.vec[P_F64].rhs_bytes();
+        OV_CUDA(c, launch_pack(c->g, src, sub, 0, st));
+        OV_CUDA(c, cudaStreamSynchronize(st));
+    }
+    E.nev = nev;
+    E.vals.assign(vals, vals + nev);
+    std::vector<double> sg(nev);
+    for (int i = 0; i < nev; ++i) sg[i] = vals[i] > 0 ? 1.0 : (vals[i] < 0 ? -1.0 : 0.0);
+    void* p = nullptr;
+    OV_TRY(dev_alloc(c, &p, sizeof(double) * nev));
+    E.d_sign = (double*)p;
+    OV_CUDA(c, cudaMemcpy(E.d_sign, sg.data(), sizeof(double) * nev, cudaMemcpyHostToDevice));
+    return OV_OK;
+}
+
+int ov_get_eigenpairs(ov_ctx* c, int which, int* nev, double* vals, void* vecs, void* stream)
+{
+    if (!c || !nev) return c ? set_err(c, OV_EINVAL, "null nev") : OV_EINVAL;
+    if (which != 0 && which != 1) return set_err(c, OV_EINVAL, "which = %d (0 or 1)", which);
+    cudaStream_t st = (cudaStream_t)stream;
+    EigSet& E = c->eig[which];
+    *nev = E.nev;
+    if (vals)
+        for (int i = 0; i < E.nev; ++i) vals[i] = E.vals[i];
+    if (vecs && E.nev) {
+        const size_t one = (size_t)2 * c->g.Vh * 12 * 16;
+        for (int i0 = 0; i0 < E.nev; i0 += 16) {
+            int n = E.nev - i0 < 16 ? E.nev - i0 : 16;
+            double* dst = nullptr;
+            void* hdst = (char*)vecs + one * i0;
+            OV_TRY(stage_out_buffer(c, 1, hdst, one * n, &dst));
+            FieldDesc sub = E.vec[P_F64];
+            sub.nrhs = n;
+            sub.data = E.vec[P_F64].data + (size_t)i0 * E.vec[P_F64].rhs_bytes();
+            OV_CUDA(c, launch_unpack(c->g, sub, dst, 0, st));
+            OV_TRY(stage_out_finish(c, hdst, dst, one * n, st));
+        }
+        OV_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return OV_OK;
+}
+
+int ov_deflate(ov_ctx* c, int which, int nev, double tol, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (which != 0 && which != 1) return set_err(c, OV_EINVAL, "which = %d (0 or 1)", which);
+    if (nev < 1 || nev > 1024) return set_err(c, OV_EINVAL, "nev = %d out of range 1..1024", nev);
+    if (!(tol > 0)) return set_err(c, OV_EINVAL, "tol must be positive");
+    if (!c->have_gauge) return set_err(c, OV_ESTATE, "deflate: no gauge field");
+    if (which == 1 && !c->have_poly) return set_err(c, OV_ESTATE, "deflate(which=1): no sign polynomial");
+    return deflate_impl(c, which, nev, tol, (cudaStream_t)stream);
+}
+
+int ov_cg_solve(ov_ctx* c, const void* b, void* x, int nrhs, double mass, double tol, int max_iter, int precond,
+                int inner_prec, ov_solve_info* info, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (!b || !x) return set_err(c, OV_EINVAL, "null buffer");
+    if (b == x) return set_err(c, OV_EINVAL, "b and x must differ");
+    if (nrhs < 1 || nrhs > 16) return set_err(c, OV_EINVAL, "nrhs = %d out of range 1..16", nrhs);
+    if (!(tol > 0) || max_iter < 1) return set_err(c, OV_EINVAL, "tol and max_iter must be positive");
+    OV_TRY(check_prec(c, inner_prec));
+    if (!c->have_gauge || !c->have_poly) return set_err(c, OV_ESTATE, "cg: needs gauge field and sign polynomial");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)nrhs * 2 * c->g.Vh * 12 * 16;
+    const double* db = nullptr;
+    double* dx = nullptr;
+    OV_TRY(stage_in(c, 0, b, bytes, st, &db));
+    OV_TRY(stage_out_buffer(c, 1, x, bytes, &dx));
+    FieldDesc fb, fx;
+    OV_TRY(ws_field(c, WS_CG_B, P_F64, nrhs, &fb));
+    OV_TRY(ws_field(c, WS_CG_X, P_F64, nrhs, &fx));
+    OV_CUDA(c, launch_pack(c->g, db, fb, 0, st));
+    int s = cg_impl(c, fb, fx, mass, tol, max_iter, precond, inner_prec, info, st);
+    if (s != OV_OK && s != OV_ENOTCONV && s != OV_ESTALL) return s;
+    OV_CUDA(c, launch_unpack(c->g, fx, dx, 0, st));
+    OV_TRY(stage_out_finish(c, x, dx, bytes, st));
+    return s;
+}
+
+int ov_field_create(ov_ctx* c, int nrhs, int prec, ov_field** f)
+{
+    if (!c || !f) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    OV_TRY(check_prec(c, prec));
+    if (nrhs < 1 || nrhs > 16) return set_err(c, OV_EINVAL, "nrhs = %d out of range 1..16", nrhs);
+    ov_field* h = new ov_field();
+    h->owner = c;
+    int s = field_alloc(c, prec, nrhs, &h->d);
+    if (s != OV_OK) {
+        delete h;
+        return s;
+    }
+    *f = h;
+    return OV_OK;
+}
+
+int ov_field_destroy(ov_field* f)
+{
+    if (!f) return OV_EINVAL;
+    cudaDeviceSynchronize();
+    field_free(f->owner, &f->d);
+    delete f;
+    return OV_OK;
+}
+
+int ov_field_import(ov_ctx* c, ov_field* f, const void* canonical, void* stream)
+{
+    if (!c || !f || !canonical) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)f->d.nrhs * 2 * c->g.Vh * 12 * 16;
+    const double* src = nullptr;
+    OV_TRY(stage_in(c, 0, canonical, bytes, st, &src));
+    OV_CUDA(c, launch_pack(c->g, src, f->d, 0, st));
+    return OV_OK;
+}
+
+int ov_field_export(ov_ctx* c, const ov_field* f, void* canonical, void* stream)
+{
+    if (!c || !f || !canonical) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)f->d.nrhs * 2 * c->g.Vh * 12 * 16;
+    double* dst = nullptr;
+    OV_TRY(stage_out_buffer(c, 1, canonical, bytes, &dst));
+    OV_CUDA(c, launch_unpack(c->g, f->d, dst, 0, st));
+    return stage_out_finish(c, canonical, dst, bytes, st);
+}
+
+int ov_dslash_field(ov_ctx* c, const ov_field* in, ov_field* out, double m, int gamma5, void* stream)
+{
+    if (!c || !in || !out) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    if (in == out) return set_err(c, OV_EINVAL, "in and out must differ");
+    if (in->d.prec != out->d.prec || in->d.nrhs != out->d.nrhs)
+        return set_err(c, OV_EINVAL, "fields differ in precision or nrhs");
+    if (!c->have_gauge) return set_err(c, OV_ESTATE, "no gauge field");
+    return dslash_apply(c, in->d, out->d, 4.0 + m, -0.5, gamma5 ? 1 : 0, 0, 0, nullptr, nullptr,
+                        (cudaStream_t)stream);
+}
+
+int ov_overlap_field(ov_ctx* c, const ov_field* in, ov_field* out, double mass, void* stream)
+{
+    if (!c || !in || !out) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    if (in == out) return set_err(c, OV_EINVAL, "in and out must differ");
+    if (in->d.prec != out->d.prec || in->d.nrhs != out->d.nrhs)
+        return set_err(c, OV_EINVAL, "fields differ in precision or nrhs");
+    return overlap_apply(c, in->d, out->d, mass, (cudaStream_t)stream);
+}
+
+long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
+
+int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by)
+{
+    if (!c) return OV_EINVAL;
+    OV_TRY(check_prec(c, prec));
+    if (bx < 1 || by < 1 || bx * by > (prec == P_F64 ? 256 : 512) || bx % 32)
+        return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
+    c->shape[{prec, nrhs}] = {bx, by};
+    return OV_OK;
+}
+
+int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    OV_TRY(check_prec(c, prec));
+    if (nrhs < 1 || nrhs > 16) return set_err(c, OV_EINVAL, "nrhs out of range");
+    if (!c->have_gauge) return set_err(c, OV_ESTATE, "no gauge field");
+    cudaStream_t st = (cudaStream_t)stream;
+    FieldDesc fi, fo;
+    OV_TRY(ws_field(c, WS_IN, prec, nrhs, &fi));
+    OV_TRY(ws_field(c, WS_OUT, prec, nrhs, &fo));
+    OV_CUDA(c, cudaMemsetAsync(fi.data, 0, data_bytes(prec, nrhs, c->g.Vh), st));
+    if (fi.norm) OV_CUDA(c, cudaMemsetAsync(fi.norm, 0, norm_bytes(prec, nrhs, c->g.Vh), st));
+    std::vector<std::pair<int, int>> cand;
+    for (int x : {32, 64, 128, 256})
+        for (int y = 1; y <= nrhs && y <= 16; ++y) {
+            if (nrhs % y && y != nrhs) continue;
+            if (x * y > (prec == P_F64 ? 256 : 512) || x * y < 64) continue;
+            cand.push_back({x, y});
+        }
+    if (cand.empty()) cand.push_back(default_shape(prec, nrhs));
+    cudaEvent_t e0, e1;
+    OV_CUDA(c, cudaEventCreate(&e0));
+    OV_CUDA(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    std::pair<int, int> bsh = cand[0];
+    for (auto sh : cand) {
+        c->shape[{prec, nrhs}] = sh;
+        OV_TRY(dslash_apply(c, fi, fo, 4.0, -0.5, 0, 0, 0, nullptr, nullptr, st));
+        OV_CUDA(c, cudaEventRecord(e0, st));
+        for (int i = 0; i < 5; ++i) OV_TRY(dslash_apply(c, fi, fo, 4.0, -0.5, 0, 0, 0, nullptr, nullptr, st));
+        OV_CUDA(c, cudaEventRecord(e1, st));
+        OV_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0;
+        OV_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bsh = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape[{prec, nrhs}] = bsh;
+    if (bx) *bx = bsh.first;
+    if (by) *by = bsh.second;
+    return OV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Library context (host side) shared by the API and solver translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/overlap.h"
+#include "ov_internal.cuh"
+#include "ov_kernels.h"
+
+struct ov_field {
+    ov::FieldDesc d;
+    ov_ctx* owner;
+};
+
+namespace ov {
+
+// workspace slots (internal fields cached per (slot, prec, nrhs))
+// device scalar scratch (c->dscal, doubles): coefficient blocks, then CG scalars
+constexpr int DSCAL_DOUBLES = 65536;
+constexpr int DSCAL_COEF = 57344;   // [0, DSCAL_COEF): coefficient blocks (double2 pairs)
+constexpr int DSCAL_CGCO = 57344;   // double2 [K][R] per-rhs coefficients
+constexpr int DSCAL_NORM = 61440;   // per-rhs norms
+constexpr int DSCAL_DOT = 62464;    // per-rhs dots (double2)
+constexpr int DSCAL_TMP = 64512;    // single-value scratch
+
+enum Slot {
+    WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
+    WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
+    WS_LZ_W, WS_LZ_T, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
+    WS_COUNT
+};
+
+struct EigSet {
+    int nev = 0;
+    std::vector<double> vals;   // host copy
+    FieldDesc vec[4] = {};      // per storage precision (F64 is the master copy)
+    double* d_sign = nullptr;   // device sign(lam_i) (which = 0)
+};
+
+struct NetState;  // learned preconditioner (net.cu)
+
+}  // namespace ov
+
+struct ov_ctx {
+    int dims[4];
+    double bc[4];
+    ov::Geom g;
+    int device = 0;
+    long long bytes = 0;
+
+    void* gauge[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool have_gauge = false;
+
+    double rho = 1.5, eps = 0.05, lmax = 0.0;
+    int degree = 0;
+    std::vector<double> coef;
+    bool have_poly = false;
+
+    ov::EigSet eig[2];
+
+    std::map<std::tuple<int, int, int>, ov::FieldDesc> ws;
+    double* partials = nullptr;
+    size_t partials_bytes = 0;
+    double* dscal = nullptr;  // device scalar scratch, DSCAL_DOUBLES doubles
+    void* stage[2] = {nullptr, nullptr};
+    size_t stage_bytes[2] = {0, 0};
+    unsigned* derr = nullptr;
+
+    std::map<std::pair<int, int>, std::pair<int, int>> shape;  // (prec, nrhs) -> (bx, by)
+
+    ov::NetState* net = nullptr;
+
+    // instrumentation: number of dslash launches issued through this context
+    long long dslash_launches = 0;
+
+    std::string err;
+};
+
+namespace ov {
+
+int set_err(ov_ctx* c, int code, const char* fmt, ...);
+#define OV_CUDA(ctx, call)                                                                         \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return ov::set_err(ctx, e_ == cudaErrorMemoryAllocation ? OV_ENOMEM : OV_ECUDA,        \
+                               "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+#define OV_TRY(x)                 \
+    do {                          \
+        int s_ = (x);             \
+        if (s_ != OV_OK) return s_; \
+    } while (0)
+
+int dev_alloc(ov_ctx* c, void** p, size_t bytes);
+void dev_free(ov_ctx* c, void* p, size_t bytes);
+int field_alloc(ov_ctx* c, int prec, int nrhs, FieldDesc* f);
+void field_free(ov_ctx* c, FieldDesc* f);
+int ws_field(ov_ctx* c, int slot, int prec, int nrhs, FieldDesc* f);
+int ensure_partials(ov_ctx* c, size_t bytes);
+bool is_device_ptr(const void* p);
+int stage_in(ov_ctx* c, int which, const void* src, size_t bytes, cudaStream_t st, const double** dev);
+int stage_out_buffer(ov_ctx* c, int which, void* dst, size_t bytes, double** dev);
+int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cudaStream_t st);
+int gauge_prec_for(int prec);
+int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out);
+
+// operators on internal fields
+int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a, double b, int g5_core, int g5_out,
+                 int ny, const FieldDesc* y, const double* sy, cudaStream_t st, int gprec = -1);
+int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
+// out = D(m)^dag D(m) in
+int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
+
+// level-1 helpers (stream-ordered); results of reductions land in device memory
+int lincomb(ov_ctx* c, const FieldDesc& out, int K, const FieldDesc* x, const double2* hcoef, const double2* dcoef,
+            int g5mask, double* dnorm_out, cudaStream_t st);
+int dot(ov_ctx* c, const FieldDesc& x, const FieldDesc& y, double2* dout, cudaStream_t st);
+int norm2(ov_ctx* c, const FieldDesc& x, double* dout, cudaStream_t st);
+int convert(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st);
+int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st);
+
+// solvers (solver.cu)
+int estimate_lambda_max(ov_ctx* c, int steps, double* lmax, cudaStream_t st);
+int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st);
+int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
+            int inner_prec, ov_solve_info* info, cudaStream_t st);
+void net_free(ov_ctx* c);
+
+}  // namespace ov

@@ -1,0 +1,243 @@
+// Internal definitions of the GB300 overlap-fermion library: lattice
+// geometry, the even/odd storage formats and their load/store routines.
+//
+// Canonical (user-facing) layout: complex128 [rhs][t][z][y][x][spin 4][colour 3],
+// gauge complex128 [t][z][y][x][mu 4][3][3], mu = 0..3 <-> x, y, z, t.
+//
+// Internal layout (library-owned).  Sites are split by parity
+// p = (x+y+z+t) & 1 and numbered within a parity by the checkerboard index
+// s = (((t*Lz + z)*Ly + y)*Lx + x) / 2 (Lx even).  A spinor field of R
+// right-hand sides is an array of 16-byte chunks
+//     chunk[r][p][k][s],  k = 0 .. NCH-1,
+// so a warp reading chunk k of 32 consecutive sites issues one coalesced
+// 512-byte transaction.  The 24 reals of a site are ordered
+// (spin, colour, re/im) and packed as 12 double2 (FP64), 6 float4 (FP32) or
+// 3 x 8 16-bit values (FP16 / BF16) with one FP32 scale per site
+// (norm[r][p][s] = max |component|, values stored divided by it).
+// Gauge links keep only rows 0 and 1 of each SU(3) matrix (reconstruct-12),
+// forward links only: link[p][mu][k][s] = U_mu(n), n = site (p, s); chunks
+// are 6 double2 (FP64), 3 float4 (FP32) or 3 x 4 16-bit values.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace ov {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+inline int spinor_chunks(int prec) { return prec == P_F64 ? 12 : (prec == P_F32 ? 6 : 3); }
+inline bool has_norm(int prec) { return prec == P_F16 || prec == P_BF16; }
+inline size_t spinor_site_bytes(int prec) { return (size_t)spinor_chunks(prec) * 16; }
+inline size_t gauge_link_bytes(int prec) { return prec == P_F64 ? 96 : (prec == P_F32 ? 48 : 24); }
+template <int P>
+__host__ __device__ constexpr size_t gauge_link_bytes_dev() { return P == P_F64 ? 96 : (P == P_F32 ? 48 : 24); }
+template <int P>
+__host__ __device__ constexpr int nchunk_dev() { return P == P_F64 ? 12 : (P == P_F32 ? 6 : 3); }
+
+struct Geom {
+    int L[4];   // Lx, Ly, Lz, Lt
+    int Lxh;    // Lx / 2
+    int Vh;     // sites per parity
+    double bc[4];
+};
+
+// A field of nrhs right-hand sides in the internal layout of one precision.
+struct FieldDesc {
+    int prec;
+    int nrhs;
+    int Vh;
+    char* data;   // [nrhs][2][NCH][Vh] x 16 bytes
+    float* norm;  // [nrhs][2][Vh] (16-bit formats), else null
+    size_t parity_bytes() const { return (size_t)spinor_chunks(prec) * 16 * Vh; }
+    size_t rhs_bytes() const { return 2 * parity_bytes(); }
+    char* ptr(int r, int p) const { return data + r * rhs_bytes() + p * parity_bytes(); }
+    float* nptr(int r, int p) const { return norm ? norm + ((size_t)r * 2 + p) * Vh : nullptr; }
+};
+
+// ---------------------------------------------------------------------------
+// geometry on the device
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cb_coords(const Geom& g, int s, int p, int c[4])
+{
+    int xh = s % g.Lxh;
+    int r = s / g.Lxh;
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+    c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
+}
+
+__device__ __forceinline__ int cb_index(const Geom& g, int x, int y, int z, int t)
+{
+    return ((t * g.L[2] + z) * g.L[1] + y) * g.Lxh + (x >> 1);
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit helpers
+// ---------------------------------------------------------------------------
+template <int P> struct Half;
+template <> struct Half<P_F16> {
+    __device__ static __forceinline__ float2 to2(uint32_t w)
+    {
+        __half2 h = *reinterpret_cast<__half2*>(&w);
+        return __half22float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+};
+template <> struct Half<P_BF16> {
+    __device__ static __forceinline__ float2 to2(uint32_t w)
+    {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+        return __bfloat1622float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from2(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// spinor load / store: v[24] = (spin, colour, re/im)
+// `base` points at chunk 0 of one (rhs, parity); `nrm` at its norm array.
+// ---------------------------------------------------------------------------
+template <int P, typename Real>
+__device__ __forceinline__ void load_spinor(const char* __restrict__ base, const float* __restrict__ nrm,
+                                            int Vh, int s, Real v[24])
+{
+    if constexpr (P == P_F64) {
+        const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 t = __ldg(b + (size_t)k * Vh + s);
+            v[2 * k] = (Real)t.x;
+            v[2 * k + 1] = (Real)t.y;
+        }
+    } else if constexpr (P == P_F32) {
+        const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 t = __ldg(b + (size_t)k * Vh + s);
+            v[4 * k] = t.x;
+            v[4 * k + 1] = t.y;
+            v[4 * k + 2] = t.z;
+            v[4 * k + 3] = t.w;
+        }
+    } else {
+        const uint4* b = reinterpret_cast<const uint4*>(base);
+        float n = __ldg(nrm + s);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t = __ldg(b + (size_t)k * Vh + s);
+            float2 a0 = Half<P>::to2(t.x), a1 = Half<P>::to2(t.y), a2 = Half<P>::to2(t.z),
+                   a3 = Half<P>::to2(t.w);
+            v[8 * k + 0] = a0.x * n;
+            v[8 * k + 1] = a0.y * n;
+            v[8 * k + 2] = a1.x * n;
+            v[8 * k + 3] = a1.y * n;
+            v[8 * k + 4] = a2.x * n;
+            v[8 * k + 5] = a2.y * n;
+            v[8 * k + 6] = a3.x * n;
+            v[8 * k + 7] = a3.y * n;
+        }
+    }
+}
+
+template <int P, typename Real>
+__device__ __forceinline__ void store_spinor(char* __restrict__ base, float* __restrict__ nrm, int Vh, int s,
+                                             const Real v[24])
+{
+    if constexpr (P == P_F64) {
+        double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) b[(size_t)k * Vh + s] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+    } else if constexpr (P == P_F32) {
+        float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            b[(size_t)k * Vh + s] =
+                make_float4((float)v[4 * k], (float)v[4 * k + 1], (float)v[4 * k + 2], (float)v[4 * k + 3]);
+    } else {
+        float m = 0.f;
+#pragma unroll
+        for (int i = 0; i < 24; ++i) m = fmaxf(m, fabsf((float)v[i]));
+        float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4* b = reinterpret_cast<uint4*>(base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t;
+            t.x = Half<P>::from2((float)v[8 * k + 0] * inv, (float)v[8 * k + 1] * inv);
+            t.y = Half<P>::from2((float)v[8 * k + 2] * inv, (float)v[8 * k + 3] * inv);
+            t.z = Half<P>::from2((float)v[8 * k + 4] * inv, (float)v[8 * k + 5] * inv);
+            t.w = Half<P>::from2((float)v[8 * k + 6] * inv, (float)v[8 * k + 7] * inv);
+            b[(size_t)k * Vh + s] = t;
+        }
+        nrm[s] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gauge link load with reconstruct-12: u[18] = 3x3 complex, row-major
+// `base` points at link[p][mu] chunk 0.
+// ---------------------------------------------------------------------------
+template <int P, typename Real>
+__device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh, int s, Real u[18])
+{
+    if constexpr (P == P_F64) {
+        const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            double2 t = __ldg(b + (size_t)k * Vh + s);
+            u[2 * k] = (Real)t.x;
+            u[2 * k + 1] = (Real)t.y;
+        }
+    } else if constexpr (P == P_F32) {
+        const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 t = __ldg(b + (size_t)k * Vh + s);
+            u[4 * k] = t.x;
+            u[4 * k + 1] = t.y;
+            u[4 * k + 2] = t.z;
+            u[4 * k + 3] = t.w;
+        }
+    } else {
+        const uint2* b = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint2 t = __ldg(b + (size_t)k * Vh + s);
+            float2 a0 = Half<P>::to2(t.x), a1 = Half<P>::to2(t.y);
+            u[4 * k] = a0.x;
+            u[4 * k + 1] = a0.y;
+            u[4 * k + 2] = a1.x;
+            u[4 * k + 3] = a1.y;
+        }
+    }
+    // row 2 = conj(row0 x row1)  (unitarity and det = 1)
+    // (r0 x r1)_0 = r0_1 r1_2 - r0_2 r1_1, _1 = r0_2 r1_0 - r0_0 r1_2, _2 = r0_0 r1_1 - r0_1 r1_0
+#define OV_RE(i) u[2 * (i)]
+#define OV_IM(i) u[2 * (i) + 1]
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        int a = (j + 1) % 3, b = (j + 2) % 3;
+        // r0_a r1_b - r0_b r1_a
+        Real re = OV_RE(a) * OV_RE(3 + b) - OV_IM(a) * OV_IM(3 + b) - (OV_RE(b) * OV_RE(3 + a) - OV_IM(b) * OV_IM(3 + a));
+        Real im = OV_RE(a) * OV_IM(3 + b) + OV_IM(a) * OV_RE(3 + b) - (OV_RE(b) * OV_IM(3 + a) + OV_IM(b) * OV_RE(3 + a));
+        u[12 + 2 * j] = re;
+        u[12 + 2 * j + 1] = -im;
+    }
+#undef OV_RE
+#undef OV_IM
+}
+
+}  // namespace ov

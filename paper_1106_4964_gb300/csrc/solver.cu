@@ -1,0 +1,774 @@
+// Solvers of the hot path, host logic over the library's kernels:
+//  * estimate_lambda_max: Lanczos on H_w^2 for ||H_w|| (the spectral rescale Q = H_w / ||H_w||, Eq. 5);
+//  * deflate_impl: thick-restart Lanczos with full FP64 Gram-Schmidt (CGS2), on a Chebyshev filter
+//    T_K(Y(A)) of A = H_w^2 (Sec. V: Chebyshev acceleration, eigenvectors of T_n(H_w^2)) or of
+//    A = D^dag D, then Rayleigh-Ritz in the converged subspace (signed eigenvalues of H_w for Eq. 7);
+//  * cg_impl: deflated CG on D(m)^dag D(m) (Eq. 9) with mixed precision and FP64 reliable updates,
+//    optionally preconditioned by the learned network (flexible CG, net.cu).
+// The paper uses implicitly restarted Arnoldi; the operators here are Hermitian, so the Lanczos form
+// of the same restarted Krylov method is used (k = l + dl basis vectors, Sec. V).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "ctx.h"
+
+namespace ov {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// dense Hermitian eigensolver (cyclic Jacobi with complex rotations)
+// A: n x n row-major Hermitian (destroyed).  ev ascending; Z[k*n + i] = component k of eigenvector i.
+// ---------------------------------------------------------------------------
+void herm_eig(int n, std::vector<cd>& A, std::vector<double>& ev, std::vector<cd>& Z)
+{
+    Z.assign((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0, tot = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = std::norm(A[(size_t)p * n + q]);
+                tot += a;
+                if (p != q) off += a;
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                cd apq = A[(size_t)p * n + q];
+                double b = std::abs(apq);
+                if (b == 0.0) continue;
+                double al = A[(size_t)p * n + p].real(), be = A[(size_t)q * n + q].real();
+                if (sweep > 3 && b < 1e-18 * (std::fabs(al) + std::fabs(be))) {
+                    A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+                    continue;
+                }
+                cd u = apq / b, uc = std::conj(u);
+                double zeta = (be - al) / (2.0 * b);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(zeta * zeta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    cd akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * uc * akq;
+                    A[(size_t)k * n + q] = s * akp + c * uc * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    cd apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * u * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * u * aqk;
+                }
+                A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+                A[(size_t)p * n + p] = al - t * b;
+                A[(size_t)q * n + q] = be + t * b;
+                for (int k = 0; k < n; ++k) {
+                    cd zkp = Z[(size_t)k * n + p], zkq = Z[(size_t)k * n + q];
+                    Z[(size_t)k * n + p] = c * zkp - s * uc * zkq;
+                    Z[(size_t)k * n + q] = s * zkp + c * uc * zkq;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(),
+              [&](int a, int b) { return A[(size_t)a * n + a].real() < A[(size_t)b * n + b].real(); });
+    ev.resize(n);
+    std::vector<cd> Zs((size_t)n * n);
+    for (int i = 0; i < n; ++i) {
+        ev[i] = A[(size_t)idx[i] * n + idx[i]].real();
+        for (int k = 0; k < n; ++k) Zs[(size_t)k * n + i] = Z[(size_t)k * n + idx[i]];
+    }
+    Z.swap(Zs);
+}
+
+namespace {
+
+FieldDesc sub(const FieldDesc& f, int i, int n = 1)
+{
+    FieldDesc s = f;
+    s.nrhs = n;
+    s.data = f.data + (size_t)i * f.rhs_bytes();
+    s.norm = f.norm ? f.norm + (size_t)i * 2 * f.Vh : nullptr;
+    return s;
+}
+
+int to_host(ov_ctx* c, const void* d, void* h, size_t bytes, cudaStream_t st)
+{
+    OV_CUDA(c, cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    return OV_OK;
+}
+
+int to_dev(ov_ctx* c, const void* h, void* d, size_t bytes, cudaStream_t st)
+{
+    OV_CUDA(c, cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
+    return OV_OK;
+}
+
+// h[i][r] = basis_i^dag w_r for i < n  (device result in c->dscal as double2 [n][R])
+int block_dots(ov_ctx* c, const FieldDesc& basis, int n, const FieldDesc& w, cudaStream_t st)
+{
+    const int nblk = reduce_blocks(c->g);
+    const int nparts = nblk * proj_groups(w.nrhs);
+    const size_t ncoef = (size_t)n * w.nrhs;
+    if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "block of %zu coefficients too large", ncoef);
+    OV_TRY(ensure_partials(c, nparts * ncoef * sizeof(double2)));
+    OV_CUDA(c, launch_proj_dots(c->g, basis, n, w, (double2*)c->partials, nblk, st));
+    OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, (double2*)c->dscal, st));
+    return OV_OK;
+}
+
+// w_r -= sum_i basis_i coef[i][r], coef (device double2 [n][R]) in c->dscal
+int block_sub(ov_ctx* c, const FieldDesc& basis, int n, const FieldDesc& w, cudaStream_t st)
+{
+    FieldDesc none{};
+    OV_CUDA(c, launch_proj_update(c->g, basis, n, (const double2*)c->dscal, nullptr, w, w, none, st));
+    return OV_OK;
+}
+
+// out_j = sum_i basis_i Y[i][j] for j < k (Y host, n x k, ld = ldy), through the zero field `zero` (16 rhs)
+int rotate(ov_ctx* c, const FieldDesc& basis, int n, const std::vector<cd>& Y, int ldy, int k, const FieldDesc& out,
+           const FieldDesc& zero, cudaStream_t st)
+{
+    for (int j0 = 0; j0 < k; j0 += 16) {
+        const int nr = std::min(16, k - j0);
+        std::vector<double2> coef((size_t)n * nr);
+        for (int i = 0; i < n; ++i)
+            for (int r = 0; r < nr; ++r) {
+                cd y = Y[(size_t)i * ldy + j0 + r];
+                coef[(size_t)i * nr + r] = make_double2(-y.real(), -y.imag());
+            }
+        if (coef.size() * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "rotation block too large");
+        OV_TRY(to_dev(c, coef.data(), c->dscal, coef.size() * sizeof(double2), st));
+        FieldDesc z = sub(zero, 0, nr), o = sub(out, j0, nr);
+        FieldDesc none{};
+        OV_CUDA(c, launch_proj_update(c->g, basis, n, (const double2*)c->dscal, nullptr, z, o, none, st));
+        OV_CUDA(c, cudaStreamSynchronize(st));  // c->dscal is reused by the next block
+    }
+    return OV_OK;
+}
+
+double host_norm(ov_ctx* c, const FieldDesc& x, cudaStream_t st, int* status)
+{
+    *status = norm2(c, x, c->dscal + DSCAL_TMP, st);
+    if (*status != OV_OK) return 0;
+    double2 v;
+    *status = to_host(c, c->dscal + DSCAL_TMP, &v, sizeof v, st);
+    return std::sqrt(v.x);
+}
+
+int scale_into(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double s, cudaStream_t st)
+{
+    double2 h = make_double2(s, 0);
+    return lincomb(c, out, 1, &in, &h, nullptr, 0, nullptr, st);
+}
+
+using OpFn = std::function<int(const FieldDesc&, const FieldDesc&)>;
+
+// Chebyshev filter: out = T_K(Y) in, Y = (2 A - (a+b)) / (b-a), three-term recurrence
+int cheb_filter(ov_ctx* c, const OpFn& A, int K, double a, double b, const FieldDesc& in, const FieldDesc& out,
+                FieldDesc tmp[3], cudaStream_t st)
+{
+    if (K == 0) return copy_field(c, in, out, st);
+    const double s1 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
+    // y1 = Y in
+    FieldDesc q = tmp[0];
+    OV_TRY(A(in, q));
+    FieldDesc prev = tmp[1], cur = tmp[2];
+    OV_TRY(copy_field(c, in, prev, st));
+    {
+        FieldDesc xs[2] = {q, in};
+        double2 h[2] = {make_double2(s1, 0), make_double2(s0, 0)};
+        OV_TRY(lincomb(c, K == 1 ? out : cur, 2, xs, h, nullptr, 0, nullptr, st));
+    }
+    if (K == 1) return OV_OK;
+    for (int j = 1; j < K; ++j) {
+        OV_TRY(A(cur, q));
+        FieldDesc dst = j == K - 1 ? out : prev;  // y_{j+1} overwrites y_{j-1}
+        FieldDesc xs[3] = {q, cur, prev};
+        double2 h[3] = {make_double2(2 * s1, 0), make_double2(2 * s0, 0), make_double2(-1, 0)};
+        OV_TRY(lincomb(c, dst, 3, xs, h, nullptr, 0, nullptr, st));
+        if (j < K - 1) std::swap(prev, cur);
+    }
+    return OV_OK;
+}
+
+// Full CGS2 of w against basis[0..n): returns the coefficient sum in h (host)
+int cgs2(ov_ctx* c, const FieldDesc& basis, int n, const FieldDesc& w, std::vector<cd>& h, cudaStream_t st)
+{
+    h.assign(n, cd(0, 0));
+    for (int pass = 0; pass < 2; ++pass) {
+        OV_TRY(block_dots(c, basis, n, w, st));
+        std::vector<double2> hh(n);
+        OV_TRY(to_host(c, c->dscal, hh.data(), n * sizeof(double2), st));
+        for (int i = 0; i < n; ++i) h[i] += cd(hh[i].x, hh[i].y);
+        OV_TRY(block_sub(c, basis, n, w, st));
+    }
+    return OV_OK;
+}
+
+// m-step Lanczos with full reorthogonalisation on a Hermitian operator; returns the Ritz values
+int plain_lanczos(ov_ctx* c, const OpFn& A, int m, const FieldDesc& basis, const FieldDesc& w, unsigned long long seed,
+                  std::vector<double>& ritz, cudaStream_t st)
+{
+    int status = OV_OK;
+    OV_CUDA(c, launch_fill_random(c->g, sub(basis, 0), seed, st));
+    double nr = host_norm(c, sub(basis, 0), st, &status);
+    OV_TRY(status);
+    OV_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
+    std::vector<cd> T((size_t)m * m, cd(0, 0));
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+        OV_TRY(A(sub(basis, j), w));
+        std::vector<cd> h;
+        OV_TRY(cgs2(c, basis, j + 1, w, h, st));
+        for (int i = 0; i <= j; ++i) {
+            T[(size_t)i * m + j] = h[i];
+            T[(size_t)j * m + i] = std::conj(h[i]);
+        }
+        double beta = host_norm(c, w, st, &status);
+        OV_TRY(status);
+        if (j + 1 < m) {
+            if (beta < 1e-12 * std::abs(T[(size_t)j * m + j]) + 1e-300) {
+                mm = j + 1;
+                break;
+            }
+            OV_TRY(scale_into(c, w, sub(basis, j + 1), 1.0 / beta, st));
+        }
+    }
+    std::vector<cd> Tm((size_t)mm * mm);
+    for (int i = 0; i < mm; ++i)
+        for (int j = 0; j < mm; ++j) Tm[(size_t)i * mm + j] = T[(size_t)i * m + j];
+    std::vector<cd> Z;
+    herm_eig(mm, Tm, ritz, Z);
+    return OV_OK;
+}
+
+}  // namespace
+
+int estimate_lambda_max(ov_ctx* c, int steps, double* lmax, cudaStream_t st)
+{
+    const long long N = 24LL * c->g.Vh;  // complex dimension 12 V
+    int m = (int)std::min<long long>(steps, N);
+    FieldDesc basis, w, t;
+    OV_TRY(field_alloc(c, P_F64, m, &basis));
+    int s = ws_field(c, WS_LZ_W, P_F64, 1, &w);
+    if (s == OV_OK) s = ws_field(c, WS_LZ_T, P_F64, 1, &t);
+    std::vector<double> ritz;
+    if (s == OV_OK) {
+        OpFn H2 = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            OV_TRY(dslash_apply(c, in, t, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return dslash_apply(c, t, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
+        s = plain_lanczos(c, H2, m, basis, w, 12345ull, ritz, st);
+    }
+    cudaStreamSynchronize(st);
+    field_free(c, &basis);
+    OV_TRY(s);
+    *lmax = std::sqrt(std::max(0.0, ritz.back()));
+    return OV_OK;
+}
+
+// Thick-restart Lanczos on F = T_K(Y(A)) (largest eigenvalues of F <-> smallest of A), then
+// Rayleigh-Ritz with the operator R (H_w for which = 0, A for which = 1).
+int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const long long N = 24LL * c->g.Vh;
+    if (nev >= N / 2) return set_err(c, OV_EINVAL, "nev = %d too large for a lattice of dimension %lld", nev, N);
+    int m = std::max((5 * nev) / 2, nev + 20);
+    m = (int)std::min<long long>(m, N - 1);
+    const int kkeep = std::min(m - 1, nev + (m - nev) / 3);
+    int status = OV_OK;
+    // precision of the operator: FP64 for the H_w modes; for D^dag D modes FP64 unless tol is loose
+    const int oprec = (which == 1 && tol >= 1e-7) ? P_F32 : P_F64;
+
+    FieldDesc basis{}, rot{}, zero{}, w{}, tmp[3] = {}, ta{}, tb{}, tsa{}, tsb{};
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        field_free(c, &basis);
+        field_free(c, &rot);
+    };
+    OV_TRY(field_alloc(c, P_F64, m + 1, &basis));
+    if ((status = field_alloc(c, P_F64, std::max(kkeep, 2 * nev) + 1, &rot)) != OV_OK) {
+        cleanup();
+        return status;
+    }
+#define DF_TRY(x)                   \
+    do {                            \
+        int s__ = (x);              \
+        if (s__ != OV_OK) {         \
+            cleanup();              \
+            return s__;             \
+        }                           \
+    } while (0)
+    DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &zero));
+    DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &w));
+    DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
+    DF_TRY(ws_field(c, WS_B0, P_F64, 1, &tmp[0]));
+    DF_TRY(ws_field(c, WS_B1, P_F64, 1, &tmp[1]));
+    DF_TRY(ws_field(c, WS_B2, P_F64, 1, &tmp[2]));
+    DF_TRY(ws_field(c, WS_T, P_F64, 1, &tb));
+    if (oprec != P_F64) {
+        DF_TRY(ws_field(c, WS_CG_RS, oprec, 1, &tsa));
+        DF_TRY(ws_field(c, WS_CG_QS, oprec, 1, &tsb));
+    }
+    OV_CUDA(c, cudaMemsetAsync(zero.data, 0, zero.rhs_bytes() * 16, st));
+
+    // A = H_w^2 (which = 0) or D(0)^dag D(0) (which = 1); R = H_w or A
+    OpFn A, Rop;
+    double bmax;
+    if (which == 0) {
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return dslash_apply(c, ta, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
+        Rop = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            return dslash_apply(c, in, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
+        double lm = c->lmax;
+        if (!(lm > 0)) {
+            DF_TRY(estimate_lambda_max(c, 50, &lm, st));
+            lm *= 1.01;
+        }
+        bmax = lm * lm;
+    } else {
+        // the stored H_w modes deflate the sign inside D; keep them
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            if (oprec == P_F64) return normal_apply(c, in, out, 0.0, st);
+            OV_TRY(convert(c, in, tsa, st));
+            OV_TRY(normal_apply(c, tsa, tsb, 0.0, st));
+            return convert(c, tsb, out, st);
+        };
+        Rop = A;
+        bmax = 4.0 * c->rho * c->rho * 1.01;
+    }
+    // cutoff a from an unfiltered Lanczos run: the j-th Ritz value bounds the j-th eigenvalue from above
+    std::vector<double> ritz0;
+    const int m0 = std::min(m, (int)std::min<long long>(N - 1, std::max(2 * nev + 20, 40)));
+    DF_TRY(plain_lanczos(c, A, m0, basis, w, 777ull + which, ritz0, st));
+    const int jcut = std::min((int)ritz0.size() - 1, nev + std::max(4, nev / 2));
+    double acut = ritz0[jcut];
+    if (!(acut < bmax)) acut = 0.5 * bmax;
+    const int K = which == 0 ? 100 : 8;
+    OpFn F = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+        return cheb_filter(c, A, K, acut, bmax, in, out, tmp, st);
+    };
+
+    // thick-restart Lanczos on F
+    DF_TRY(launch_fill_random(c->g, sub(basis, 0), 4242ull + which, st) == cudaSuccess ? OV_OK : OV_ECUDA);
+    {
+        double nr = host_norm(c, sub(basis, 0), st, &status);
+        DF_TRY(status);
+        DF_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
+    }
+    std::vector<cd> T((size_t)m * m, cd(0, 0));
+    std::vector<double> theta;
+    std::vector<cd> Y;
+    int k = 0;
+    double tolF = 1e-2 * tol;
+    bool done = false;
+    int restarts = 0;
+    std::vector<int> order;
+    double maxres = 0;
+    for (restarts = 0; restarts < 60 && !done; ++restarts) {
+        double beta = 0;
+        for (int j = k; j < m; ++j) {
+            DF_TRY(F(sub(basis, j), w));
+            std::vector<cd> h;
+            DF_TRY(cgs2(c, basis, j + 1, w, h, st));
+            for (int i = 0; i <= j; ++i) {
+                if (i < k && j < k) continue;
+                T[(size_t)i * m + j] = h[i];
+                T[(size_t)j * m + i] = std::conj(h[i]);
+            }
+            T[(size_t)j * m + j] = h[j].real();
+            beta = host_norm(c, w, st, &status);
+            DF_TRY(status);
+            if (beta < 1e-300) beta = 1e-300;
+            DF_TRY(scale_into(c, w, sub(basis, j + 1), 1.0 / beta, st));
+        }
+        std::vector<cd> Tc = T;
+        DF_TRY(OV_OK);
+        herm_eig(m, Tc, theta, Y);
+        // descending order of theta (largest of F = smallest of A)
+        order.resize(m);
+        for (int i = 0; i < m; ++i) order[i] = m - 1 - i;
+        const double tmax = std::fabs(theta[order[0]]);
+        int nconv = 0;
+        for (int i = 0; i < nev; ++i) {
+            double r = beta * std::abs(Y[(size_t)(m - 1) * m + order[i]]);
+            if (r <= tolF * std::max(std::fabs(theta[order[i]]), 1e-300 * tmax)) ++nconv;
+        }
+        if (nconv == nev) {
+            // Rayleigh-Ritz with R in span of the nev leading Ritz vectors, and true residuals
+            std::vector<cd> Yk((size_t)m * nev);
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < nev; ++j) Yk[(size_t)i * nev + j] = Y[(size_t)i * m + order[j]];
+            FieldDesc Z = sub(rot, 0, nev);
+            DF_TRY(rotate(c, basis, m, Yk, nev, nev, Z, zero, st));
+            FieldDesc RZ = sub(basis, 0, nev);  // basis is free now
+            for (int j = 0; j < nev; ++j) DF_TRY(Rop(sub(Z, j), sub(RZ, j)));
+            std::vector<cd> M((size_t)nev * nev);
+            for (int j0 = 0; j0 < nev; j0 += 16) {
+                int nr = std::min(16, nev - j0);
+                DF_TRY(block_dots(c, Z, nev, sub(RZ, j0, nr), st));
+                std::vector<double2> hh((size_t)nev * nr);
+                DF_TRY(to_host(c, c->dscal, hh.data(), hh.size() * sizeof(double2), st));
+                for (int i = 0; i < nev; ++i)
+                    for (int r = 0; r < nr; ++r) M[(size_t)i * nev + j0 + r] = cd(hh[(size_t)i * nr + r].x, hh[(size_t)i * nr + r].y);
+            }
+            for (int i = 0; i < nev; ++i)
+                for (int j = i; j < nev; ++j) {
+                    cd a = 0.5 * (M[(size_t)i * nev + j] + std::conj(M[(size_t)j * nev + i]));
+                    M[(size_t)i * nev + j] = a;
+                    M[(size_t)j * nev + i] = std::conj(a);
+                }
+            std::vector<double> lam;
+            std::vector<cd> S;
+            herm_eig(nev, M, lam, S);
+            // order by |lambda| (which = 0) or lambda (which = 1, all >= 0)
+            std::vector<int> o(nev);
+            for (int i = 0; i < nev; ++i) o[i] = i;
+            std::sort(o.begin(), o.end(), [&](int a, int b) { return std::fabs(lam[a]) < std::fabs(lam[b]); });
+            std::vector<cd> So((size_t)nev * nev);
+            std::vector<double> lo(nev);
+            for (int j = 0; j < nev; ++j) {
+                lo[j] = lam[o[j]];
+                for (int i = 0; i < nev; ++i) So[(size_t)i * nev + j] = S[(size_t)i * nev + o[j]];
+            }
+            FieldDesc eta = sub(basis, nev, nev), Reta = sub(rot, 0, nev);
+            DF_TRY(rotate(c, Z, nev, So, nev, nev, eta, zero, st));
+            DF_TRY(rotate(c, RZ, nev, So, nev, nev, Reta, zero, st));
+            // residuals |R eta - lam eta| / scale
+            const double scale = which == 0 ? std::sqrt(bmax) : bmax;
+            maxres = 0;
+            for (int j = 0; j < nev; ++j) {
+                FieldDesc xs[2] = {sub(Reta, j), sub(eta, j)};
+                double2 h[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
+                DF_TRY(lincomb(c, w, 2, xs, h, nullptr, 0, nullptr, st));
+                double r = host_norm(c, w, st, &status);
+                DF_TRY(status);
+                maxres = std::max(maxres, r / scale);
+            }
+            if (maxres <= tol || restarts >= 59 || tolF < 1e-15) {
+                // store
+                EigSet& E = c->eig[which];
+                for (auto& f : E.vec) field_free(c, &f);
+                if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
+                E.d_sign = nullptr;
+                E.nev = 0;
+                DF_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
+                OV_CUDA(c, cudaMemcpyAsync(E.vec[P_F64].data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice,
+                                           st));
+                E.vals = lo;
+                E.nev = nev;
+                std::vector<double> sg(nev);
+                for (int i = 0; i < nev; ++i) sg[i] = lo[i] > 0 ? 1.0 : (lo[i] < 0 ? -1.0 : 0.0);
+                void* p = nullptr;
+                DF_TRY(dev_alloc(c, &p, sizeof(double) * nev));
+                E.d_sign = (double*)p;
+                OV_CUDA(c, cudaMemcpyAsync(E.d_sign, sg.data(), sizeof(double) * nev, cudaMemcpyHostToDevice, st));
+                OV_CUDA(c, cudaStreamSynchronize(st));
+                done = true;
+                break;
+            }
+            // not accurate enough: tighten and restart from the Ritz vectors
+            tolF *= 1e-2;
+            // rebuild: basis[0..nev) = eta is not a Krylov relation of F; restart plainly from Z
+            // (put Z back into basis and restart the Krylov recurrence with k = 0 from Z_0 + ...)
+            OV_CUDA(c, cudaMemcpyAsync(basis.data, Z.data, Z.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
+            // start vector: sum of the Ritz vectors (keeps all wanted directions)
+            {
+                std::vector<cd> ones((size_t)nev, cd(1.0, 0.0));
+                DF_TRY(rotate(c, sub(basis, 0, nev), nev, ones, 1, 1, sub(rot, 0), zero, st));
+                double nr = host_norm(c, sub(rot, 0), st, &status);
+                DF_TRY(status);
+                DF_TRY(scale_into(c, sub(rot, 0), sub(basis, 0), 1.0 / nr, st));
+            }
+            std::fill(T.begin(), T.end(), cd(0, 0));
+            k = 0;
+            continue;
+        }
+        // thick restart: keep the kkeep leading Ritz vectors
+        std::vector<cd> Yk((size_t)m * kkeep);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < kkeep; ++j) Yk[(size_t)i * kkeep + j] = Y[(size_t)i * m + order[j]];
+        DF_TRY(rotate(c, basis, m, Yk, kkeep, kkeep, rot, zero, st));
+        OV_CUDA(c, cudaMemcpyAsync(basis.data, rot.data, rot.rhs_bytes() * kkeep, cudaMemcpyDeviceToDevice, st));
+        OV_CUDA(c, cudaMemcpyAsync(sub(basis, kkeep).data, sub(basis, m).data, basis.rhs_bytes(),
+                                   cudaMemcpyDeviceToDevice, st));
+        std::fill(T.begin(), T.end(), cd(0, 0));
+        for (int i = 0; i < kkeep; ++i) T[(size_t)i * m + i] = theta[order[i]];
+        k = kkeep;
+    }
+    cleanup();
+#undef DF_TRY
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    (void)secs;
+    if (!done) return set_err(c, OV_ENOTCONV, "deflate(which=%d): not converged after %d restarts", which, restarts);
+    if (maxres > tol)
+        return set_err(c, OV_ENOTCONV, "deflate(which=%d): max relative eigen-residual %.3e > tol %.3e", which, maxres,
+                       tol);
+    return OV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deflated CG with reliable updates
+// ---------------------------------------------------------------------------
+int net_apply_precond(ov_ctx* c, const FieldDesc& r, const FieldDesc& z, cudaStream_t st);
+bool net_ready(const ov_ctx* c);
+
+int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
+            int inner_prec, ov_solve_info* info, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int R = b.nrhs;
+    const int Ps = inner_prec;
+    const bool sloppy = Ps != P_F64;
+    if (precond && !net_ready(c)) return set_err(c, OV_ESTATE, "cg: learned preconditioner requested but not trained");
+    EigSet& X = c->eig[1];
+    const int nd = X.nev;
+    FieldDesc r, t, rs, ps, qs, xs, xt, zs, rold, zero;
+    OV_TRY(ws_field(c, WS_CG_R, P_F64, R, &r));
+    OV_TRY(ws_field(c, WS_CG_T, P_F64, R, &t));
+    OV_TRY(ws_field(c, WS_CG_U, P_F64, R, &xt));
+    OV_TRY(ws_field(c, WS_AUX1, P_F64, 16, &zero));
+    OV_CUDA(c, cudaMemsetAsync(zero.data, 0, zero.rhs_bytes() * 16, st));
+    if (sloppy) {
+        OV_TRY(ws_field(c, WS_CG_RS, Ps, R, &rs));
+        OV_TRY(ws_field(c, WS_CG_XS, Ps, R, &xs));
+    } else {
+        rs = r;
+        OV_TRY(ws_field(c, WS_CG_XS, P_F64, R, &xs));
+    }
+    OV_TRY(ws_field(c, WS_CG_PS, Ps, R, &ps));
+    OV_TRY(ws_field(c, WS_CG_QS, Ps, R, &qs));
+    if (precond) {
+        OV_TRY(ws_field(c, WS_CG_Z, Ps, R, &zs));
+        OV_TRY(ws_field(c, WS_CG_P, Ps, R, &rold));
+    }
+    double2* dco = (double2*)(c->dscal + DSCAL_CGCO);  // per-rhs coefficients [K][R]
+    double* dnr = c->dscal + DSCAL_NORM;              // per-rhs norms
+    double2* ddt = (double2*)(c->dscal + DSCAL_DOT);   // per-rhs dots
+
+    // deflation: mu_i(m) = (rho^2 - m^2/4) mu_i / rho^2 + m^2 (D^dag D = D + D^dag for the exact sign)
+    std::vector<double> mu(nd), inv(nd, 0.0);
+    double mumax = 0;
+    for (int i = 0; i < nd; ++i) {
+        mu[i] = (c->rho * c->rho - 0.25 * mass * mass) * X.vals[i] / (c->rho * c->rho) + mass * mass;
+        mumax = std::max(mumax, mu[i]);
+    }
+    for (int i = 0; i < nd; ++i) inv[i] = mu[i] > 1e-10 * mumax ? 1.0 / mu[i] : 0.0;
+    FieldDesc xi64{}, xis{};
+    if (nd) {
+        OV_TRY(eig_vectors(c, 1, P_F64, st, &xi64));
+        OV_TRY(eig_vectors(c, 1, Ps, st, &xis));
+    }
+    auto project = [&](const FieldDesc& xiv, const FieldDesc& v) -> int {
+        if (!nd) return OV_OK;
+        OV_TRY(block_dots(c, xiv, nd, v, st));
+        return block_sub(c, xiv, nd, v, st);
+    };
+    // x0 = sum_i xi_i (xi_i^dag b) / mu_i
+    if (nd) {
+        OV_TRY(block_dots(c, xi64, nd, b, st));
+        std::vector<double2> h((size_t)nd * R);
+        OV_TRY(to_host(c, c->dscal, h.data(), h.size() * sizeof(double2), st));
+        for (int i = 0; i < nd; ++i)
+            for (int q = 0; q < R; ++q) {
+                double2& v = h[(size_t)i * R + q];
+                v = make_double2(-v.x * inv[i], -v.y * inv[i]);
+            }
+        OV_TRY(to_dev(c, h.data(), c->dscal, h.size() * sizeof(double2), st));
+        FieldDesc none{};
+        OV_CUDA(c, launch_proj_update(c->g, xi64, nd, (const double2*)c->dscal, nullptr, sub(zero, 0, R), x, none, st));
+    } else {
+        OV_CUDA(c, cudaMemsetAsync(x.data, 0, x.rhs_bytes() * R, st));
+    }
+    std::vector<double2> hb(R);
+    OV_TRY(norm2(c, b, (double*)ddt, st));
+    OV_TRY(to_host(c, ddt, hb.data(), R * sizeof(double2), st));
+    std::vector<double> bn(R);
+    for (int q = 0; q < R; ++q) bn[q] = std::sqrt(hb[q].x) > 0 ? std::sqrt(hb[q].x) : 1.0;
+
+    std::vector<double> rr(R), rr_new(R), rmax(R), res(R, 1.0), pq(R);
+    std::vector<char> done(R, 0);
+    int iters = 0, updates = 0, fallback = 0;
+    bool use_prec = precond != 0;
+    std::vector<double> hist;  // true residual history (max over rhs) for the stall rule
+
+    auto true_residual = [&](bool& all_done) -> int {
+        // r = b - A x (FP64), projected
+        OV_TRY(normal_apply(c, x, t, mass, st));
+        FieldDesc xs2[2] = {b, t};
+        double2 h2[2] = {make_double2(1, 0), make_double2(-1, 0)};
+        OV_TRY(lincomb(c, r, 2, xs2, h2, nullptr, 0, dnr, st));
+        std::vector<double> nr(R);
+        OV_TRY(to_host(c, dnr, nr.data(), R * sizeof(double), st));
+        all_done = true;
+        for (int q = 0; q < R; ++q) {
+            res[q] = std::sqrt(nr[q]) / bn[q];
+            if (res[q] <= tol) done[q] = 1;
+            if (!done[q]) all_done = false;
+        }
+        OV_TRY(project(xi64, r));
+        ++updates;
+        return OV_OK;
+    };
+    auto sloppy_norms = [&](const FieldDesc& v, std::vector<double>& out) -> int {
+        OV_TRY(norm2(c, v, (double*)ddt, st));
+        std::vector<double2> h(R);
+        OV_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+        for (int q = 0; q < R; ++q) out[q] = h[q].x;
+        return OV_OK;
+    };
+    auto set_coef = [&](int K, const std::vector<double2>& h) -> int {
+        return to_dev(c, h.data(), dco, (size_t)K * R * sizeof(double2), st);
+    };
+
+    bool all_done = false;
+    OV_TRY(true_residual(all_done));
+    const double delta = 0.1;  // reliable-update trigger: residual drop since the last update
+    if (!all_done) {
+        if (sloppy) OV_TRY(convert(c, r, rs, st));
+        OV_CUDA(c, cudaMemsetAsync(xs.data, 0, xs.rhs_bytes() * R, st));
+        if (xs.norm) OV_CUDA(c, cudaMemsetAsync(xs.norm, 0, (size_t)2 * xs.Vh * 4 * R, st));
+        OV_TRY(sloppy_norms(rs, rr));
+        for (int q = 0; q < R; ++q) rmax[q] = std::sqrt(rr[q]);
+        // p = z = M r (preconditioned) or r
+        std::vector<double> rz(R);
+        if (use_prec) {
+            OV_TRY(net_apply_precond(c, rs, zs, st));
+            OV_TRY(project(xis, zs));
+            OV_TRY(copy_field(c, zs, ps, st));
+            OV_TRY(dot(c, rs, zs, ddt, st));
+            std::vector<double2> h(R);
+            OV_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+            for (int q = 0; q < R; ++q) rz[q] = h[q].x;
+        } else {
+            OV_TRY(copy_field(c, rs, ps, st));
+            rz = rr;
+        }
+        while (iters < max_iter) {
+            OV_TRY(normal_apply(c, ps, qs, mass, st));
+            OV_TRY(dot(c, ps, qs, ddt, st));
+            std::vector<double2> h(R);
+            OV_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+            std::vector<double2> co(2 * R);
+            for (int q = 0; q < R; ++q) {
+                double a = (done[q] || h[q].x <= 0) ? 0.0 : rz[q] / h[q].x;
+                co[q] = make_double2(1, 0);
+                co[R + q] = make_double2(a, 0);
+            }
+            OV_TRY(set_coef(2, co));
+            {
+                FieldDesc v[2] = {xs, ps};
+                OV_TRY(lincomb(c, xs, 2, v, nullptr, dco, 0, nullptr, st));
+            }
+            if (use_prec) OV_TRY(copy_field(c, rs, rold, st));
+            for (int q = 0; q < R; ++q) co[R + q].x = -co[R + q].x;
+            OV_TRY(set_coef(2, co));
+            {
+                FieldDesc v[2] = {rs, qs};
+                OV_TRY(lincomb(c, rs, 2, v, nullptr, dco, 0, nullptr, st));
+            }
+            OV_TRY(project(xis, rs));
+            OV_TRY(sloppy_norms(rs, rr_new));
+            ++iters;
+            bool trigger = false;
+            for (int q = 0; q < R; ++q) {
+                if (done[q]) continue;
+                if (std::sqrt(rr_new[q]) <= tol * bn[q]) trigger = true;
+                if (sloppy && std::sqrt(rr_new[q]) < delta * rmax[q]) trigger = true;
+                if (!std::isfinite(rr_new[q])) return set_err(c, OV_ENAN, "cg: NaN/Inf in the residual");
+            }
+            if (trigger) {
+                // x += xs (FP64), true residual, restart the sloppy accumulation
+                if (sloppy) {
+                    OV_TRY(convert(c, xs, xt, st));
+                } else {
+                    OV_TRY(copy_field(c, xs, xt, st));
+                }
+                FieldDesc v[2] = {x, xt};
+                double2 h2[2] = {make_double2(1, 0), make_double2(1, 0)};
+                OV_TRY(lincomb(c, x, 2, v, h2, nullptr, 0, nullptr, st));
+                OV_CUDA(c, cudaMemsetAsync(xs.data, 0, xs.rhs_bytes() * R, st));
+                if (xs.norm) OV_CUDA(c, cudaMemsetAsync(xs.norm, 0, (size_t)2 * xs.Vh * 4 * R, st));
+                OV_TRY(true_residual(all_done));
+                double worst = 0;
+                for (int q = 0; q < R; ++q) worst = std::max(worst, res[q]);
+                hist.push_back(worst);
+                if (all_done) break;
+                if (sloppy) OV_TRY(convert(c, r, rs, st));
+                OV_TRY(sloppy_norms(rs, rr_new));
+                for (int q = 0; q < R; ++q) rmax[q] = std::sqrt(rr_new[q]);
+                // stall rule for the learned preconditioner: < x0.9 drop over 10 updates' worth
+                if (use_prec && hist.size() >= 3) {
+                    size_t n = hist.size();
+                    if (hist[n - 1] > 0.9 * hist[n - 3]) {
+                        use_prec = false;
+                        fallback = 1;
+                    }
+                }
+            }
+            // next direction
+            std::vector<double> rz_new(R);
+            if (use_prec) {
+                OV_TRY(net_apply_precond(c, rs, zs, st));
+                OV_TRY(project(xis, zs));
+                // flexible CG (Polak-Ribiere form): beta = z_new^dag (r_new - r_old) / (z_old^dag r_old)
+                FieldDesc v[2] = {rs, rold};
+                double2 h2[2] = {make_double2(1, 0), make_double2(-1, 0)};
+                OV_TRY(lincomb(c, rold, 2, v, h2, nullptr, 0, nullptr, st));
+                OV_TRY(dot(c, zs, rold, ddt, st));
+                std::vector<double2> hh(R);
+                OV_TRY(to_host(c, ddt, hh.data(), R * sizeof(double2), st));
+                OV_TRY(dot(c, rs, zs, ddt, st));
+                std::vector<double2> hz(R);
+                OV_TRY(to_host(c, ddt, hz.data(), R * sizeof(double2), st));
+                for (int q = 0; q < R; ++q) {
+                    double be = trigger ? 0.0 : (rz[q] != 0 ? hh[q].x / rz[q] : 0.0);
+                    co[q] = make_double2(1, 0);
+                    co[R + q] = make_double2(be, 0);
+                    rz_new[q] = hz[q].x;
+                }
+                OV_TRY(set_coef(2, co));
+                FieldDesc w2[2] = {zs, ps};
+                OV_TRY(lincomb(c, ps, 2, w2, nullptr, dco, 0, nullptr, st));
+            } else {
+                for (int q = 0; q < R; ++q) {
+                    double be = rr[q] > 0 ? rr_new[q] / rr[q] : 0.0;
+                    co[q] = make_double2(1, 0);
+                    co[R + q] = make_double2(be, 0);
+                    rz_new[q] = rr_new[q];
+                }
+                OV_TRY(set_coef(2, co));
+                FieldDesc w2[2] = {rs, ps};
+                OV_TRY(lincomb(c, ps, 2, w2, nullptr, dco, 0, nullptr, st));
+            }
+            rr = rr_new;
+            rz = rz_new;
+        }
+    }
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->iterations = iters;
+        info->reliable_updates = updates;
+        info->fallback = fallback;
+        info->nrhs = R;
+        for (int q = 0; q < R && q < 64; ++q) info->true_residual[q] = res[q];
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    bool ok = true;
+    for (int q = 0; q < R; ++q) ok = ok && res[q] <= tol;
+    if (!ok) return set_err(c, OV_ENOTCONV, "cg: not converged after %d iterations", iters);
+    return OV_OK;
+}
+
+}  // namespace ov

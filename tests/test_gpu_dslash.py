@@ -1,0 +1,143 @@
+"""GPU parity of the even/odd dslash and H_w (Eqs. 1-2) against the FP64 oracle,
+through the C ABI: several lattices (including a ragged last block and
+L = 2 directions), all storage precisions, multi-RHS, host and device
+buffers, the internal-field path, and sampled sites of the full 24^3 x 64
+workload in the benchmark's launch configuration."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import ABC, RHO, TOL, dev, host, need_gpu, rel, torch
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (4, 4, 6, 8), (6, 4, 4, 6), (8, 8, 8, 8), (2, 6, 4, 10)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_dslash_parity(dims, prec):
+    from paper_1106_4964_gb300 import Context
+
+    U = synth.gauge_field(dims, 1, 0.5)
+    psi = synth.gaussian_spinor(dims, 2)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    out = torch.empty_like(dev(psi))
+    ctx.apply_dslash(dev(psi), out, -RHO, prec=prec)
+    ref = oracle.dslash(dims, ABC, U, -RHO, psi)
+    err = rel(host(out), ref)
+    print(f"dslash {dims} {prec}: rel err {err:.3e}")
+    assert err <= TOL[prec]
+    ctx.apply_Hw(dev(psi), out, -RHO, prec=prec)
+    err = rel(host(out), oracle.hw(dims, ABC, U, -RHO, psi))
+    assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 12), ("f16", 5), ("f64", 12)])
+def test_multi_rhs(prec, nrhs):
+    from paper_1106_4964_gb300 import Context
+
+    dims = (4, 4, 4, 6)
+    U = synth.gauge_field(dims, 3, 0.5)
+    psi = synth.gaussian_spinor(dims, 4, nrhs=nrhs)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    out = torch.empty_like(dev(psi))
+    ctx.apply_dslash(dev(psi), out, 0.1, prec=prec)
+    got = host(out)
+    for r in range(nrhs):
+        assert rel(got[r], oracle.dslash(dims, ABC, U, 0.1, psi[r])) <= TOL[prec]
+
+
+def test_host_buffers_and_periodic_bc():
+    from paper_1106_4964_gb300 import Context
+
+    dims, bc = (4, 2, 4, 4), (1.0, 1.0, 1.0, 1.0)
+    U = synth.gauge_field(dims, 5, 0.5)
+    psi = synth.gaussian_spinor(dims, 6)
+    ctx = Context(dims, bc)
+    ctx.set_gauge(U)  # host numpy buffer
+    out = np.empty_like(psi)
+    ctx.apply_dslash(psi, out, -RHO, prec="f64")
+    assert rel(out, oracle.dslash(dims, bc, U, -RHO, psi)) <= 1e-12
+
+
+def test_field_path_matches_canonical():
+    from paper_1106_4964_gb300 import Context
+
+    dims = (6, 4, 4, 6)
+    U = synth.gauge_field(dims, 7, 0.5)
+    psi = synth.gaussian_spinor(dims, 8, nrhs=2)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    for prec in ("f64", "f32", "f16"):
+        fi, fo = ctx.field(2, prec), ctx.field(2, prec)
+        fi.load(dev(psi))
+        ctx.dslash_field(fi, fo, -RHO, gamma5=True)
+        out = torch.empty_like(dev(psi))
+        fo.store(out)
+        ref = np.stack([oracle.hw(dims, ABC, U, -RHO, psi[r]) for r in range(2)])
+        assert rel(host(out), ref) <= TOL[prec]
+
+
+def test_rejects_non_su3_gauge():
+    from paper_1106_4964_gb300 import Context, OverlapError
+
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 1, 0.3)
+    U[1, 2, 3, 0, 2] *= 1.001
+    ctx = Context(dims, ABC)
+    with pytest.raises(OverlapError) as e:
+        ctx.set_gauge(dev(U))
+    assert "SU(3)" in str(e.value)
+
+
+def test_bad_arguments():
+    from paper_1106_4964_gb300 import Context, OverlapError
+
+    with pytest.raises(OverlapError):
+        Context((3, 4, 4, 4))
+    ctx = Context((4, 4, 4, 4))
+    x = torch.zeros((1, 4, 4, 4, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(OverlapError):  # no gauge yet
+        ctx.apply_dslash(x, torch.empty_like(x), 0.0)
+    with pytest.raises(OverlapError):  # overlap needs set_sign_poly
+        ctx.set_gauge(dev(synth.unit_gauge((4, 4, 4, 4))))
+        ctx.apply_overlap(x, torch.empty_like(x))
+
+
+@pytest.fixture(scope="module")
+def big():
+    dims = (24, 24, 24, 64)
+    U = synth.gauge_field(dims, 1, 0.5, ape_steps=3)
+    psi = synth.gaussian_spinor(dims, 2)
+    return dims, U, psi
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64", "f16"])
+def test_full_size_sampled_sites(big, prec):
+    """24^3 x 64 (the benchmark workload), internal-field launch as timed by bench.py;
+    256 sampled output sites against the oracle computed site by site."""
+    from paper_1106_4964_gb300 import Context
+
+    dims, U, psi = big
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    fi, fo = ctx.field(1, prec), ctx.field(1, prec)
+    fi.load(dev(psi))
+    ctx.dslash_field(fi, fo, -RHO)
+    out = torch.empty_like(dev(psi))
+    fo.store(out)
+    got = host(out).reshape(-1, 4, 3)
+    rng = np.random.default_rng(0)
+    V = oracle.volume(dims)
+    sites = np.concatenate([[0, V - 1, V // 2], rng.integers(0, V, 253)])
+    ref = oracle.dslash_sites(dims, ABC, U, -RHO, psi, sites)
+    assert rel(got[sites], ref) <= TOL[prec]

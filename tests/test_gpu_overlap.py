@@ -1,0 +1,111 @@
+"""GPU parity of the overlap operator (Eqs. 3, 5-8) against the FP64 oracle on
+the 4^4 workload (links exp(0.3 i H), rho = 1.5, degree-100 Chebyshev on
+[0.05, 1]), with the low modes of H_w (|lambda|/lambda_max < sqrt(eps))
+deflated exactly from a dense eigendecomposition handed to both sides."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import dense
+from gpu_common import ABC, RHO, TOL, dev, host, need_gpu, rel, torch
+
+pytestmark = pytest.mark.gpu
+
+# overlap tolerances: FP64 and FP32 as for one application (spec values);
+# 16-bit storage is reported, bounded by the error growth of 2n+1 chained applications
+OTOL = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-2, "bf16": 2e-1}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def setup(dims, s, seed, eps, n, nev_cap=None):
+    U = synth.gauge_field(dims, seed, s)
+    V = oracle.volume(dims)
+    H = dense(lambda v: oracle.hw(dims, ABC, U, -RHO, v), V)
+    lam, vec = np.linalg.eigh(H)
+    lmax = 1.01 * np.abs(lam).max()
+    order = np.argsort(np.abs(lam))
+    nev = int(np.sum(np.abs(lam) / lmax < np.sqrt(eps)))
+    if nev_cap is not None:
+        nev = max(nev, nev_cap)
+    ev = lam[order[:nev]].copy()
+    eta = np.ascontiguousarray(vec[:, order[:nev]].T)
+    c = oracle.cheb_coeffs(eps, n)
+    return dict(dims=dims, U=U, lmax=lmax, eps=eps, n=n, c=c, ev=ev, eta=eta, lam=lam, vec=vec)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return setup((4, 4, 4, 4), 0.3, 1, 0.05, 100)
+
+
+def make_ctx(cf):
+    from paper_1106_4964_gb300 import Context
+
+    ctx = Context(cf["dims"], ABC)
+    ctx.set_gauge(dev(cf["U"]))
+    ctx.set_sign_poly(RHO, cf["eps"], cf["n"], cf["lmax"])
+    if len(cf["ev"]):
+        ctx.set_eigenpairs(0, cf["ev"], dev(cf["eta"]))
+    return ctx
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_overlap_parity_config1(cfg1, prec):
+    cf = cfg1
+    psi = synth.gaussian_spinor(cf["dims"], 2)
+    ctx = make_ctx(cf)
+    out = torch.empty_like(dev(psi))
+    ctx.apply_overlap(dev(psi), out, 0.0, prec=prec)
+    ref = oracle.overlap(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], psi, cf["ev"], cf["eta"])
+    err = rel(host(out), ref)
+    print(f"overlap 4^4 n=100 nev={len(cf['ev'])} {prec}: rel err {err:.3e}")
+    assert err <= OTOL[prec]
+
+
+def test_overlap_massive_multirhs():
+    cf = setup((2, 2, 4, 4), 0.6, 3, 0.02, 60)
+    psi = synth.gaussian_spinor(cf["dims"], 5, nrhs=3)
+    ctx = make_ctx(cf)
+    m = 0.1
+    for prec in ("f64", "f32"):
+        out = torch.empty_like(dev(psi))
+        ctx.apply_overlap(dev(psi), out, m, prec=prec)
+        got = host(out)
+        for r in range(3):
+            ref = oracle.overlap(cf["dims"], ABC, cf["U"], RHO, m, cf["lmax"], cf["eps"], cf["c"], psi[r], cf["ev"],
+                                 cf["eta"])
+            assert rel(got[r], ref) <= OTOL[prec]
+
+
+def test_overlap_without_deflation_and_small_degree():
+    dims = (4, 2, 2, 4)
+    U = synth.gauge_field(dims, 9, 0.4)
+    psi = synth.gaussian_spinor(dims, 10)
+    from paper_1106_4964_gb300 import Context
+
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    for n in (0, 1, 2, 3, 7):
+        ctx.set_sign_poly(RHO, 0.1, n, 7.5)
+        out = torch.empty_like(dev(psi))
+        ctx.apply_overlap(dev(psi), out, 0.0, prec="f64")
+        ref = oracle.overlap(dims, ABC, U, RHO, 0.0, 7.5, 0.1, oracle.cheb_coeffs(0.1, n), psi)
+        assert rel(host(out), ref) <= 1e-12, n
+
+
+def test_ginsparg_wilson_on_gpu(cfg1):
+    """gamma5 D + D gamma5 = D gamma5 D / rho, evaluated with the GPU operator (FP64)."""
+    cf = cfg1
+    ctx = make_ctx(cf)
+    psi = synth.gaussian_spinor(cf["dims"], 11)[0]
+    D = lambda v: host(ctx.apply_overlap(dev(v.reshape(psi.shape)), torch.empty_like(dev(psi)), 0.0)).reshape(-1)
+    g5 = lambda v: oracle.gamma5(v).reshape(-1)
+    v = psi.reshape(-1)
+    lhs = g5(D(v)) + D(g5(v))
+    rhs = D(g5(D(v))) / RHO
+    assert rel(lhs, rhs) < 1e-10

@@ -1,0 +1,114 @@
+"""GPU eigensolvers and deflated CG (Sec. V, Eq. 9) checked by the oracle:
+lambda_max against a dense eigendecomposition, the H_w and D^dag D low modes
+against dense spectra and oracle eigen-residuals, and CG solutions by their
+FP64 true residual computed with the oracle's operator."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import dense
+from gpu_common import ABC, RHO, dev, host, need_gpu, rel, torch
+from test_gpu_overlap import make_ctx, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return setup((4, 4, 4, 4), 0.3, 1, 0.05, 100)
+
+
+def test_lambda_max_estimate(cfg1):
+    from paper_1106_4964_gb300 import Context
+
+    ctx = Context(cfg1["dims"], ABC)
+    ctx.set_gauge(dev(cfg1["U"]))
+    ctx.set_sign_poly(RHO, 0.05, 10, 0.0)
+    lm = ctx.get_sign_poly()["lambda_max"]
+    assert abs(lm / cfg1["lmax"] - 1) < 1e-6
+
+
+def test_deflate_hw_modes(cfg1):
+    cf = cfg1
+    ctx = make_ctx(cf)
+    nev = 12
+    ctx.deflate(0, nev, 1e-10)
+    vals, vecs = ctx.get_eigenpairs(0)
+    exact = cf["lam"][np.argsort(np.abs(cf["lam"]))[:nev]]
+    # |lambda| order; +-lambda pairs are resolved by Rayleigh-Ritz with H_w
+    assert np.allclose(np.sort(np.abs(vals)), np.sort(np.abs(exact)), rtol=0, atol=1e-9 * cf["lmax"])
+    assert np.allclose(np.sort(vals), np.sort(exact), rtol=0, atol=1e-9 * cf["lmax"])
+    G = vecs.conj() @ vecs.T
+    assert np.abs(G - np.eye(nev)).max() < 1e-12
+    for i in range(nev):
+        r = oracle.hw(cf["dims"], ABC, cf["U"], -RHO, vecs[i]) - vals[i] * vecs[i]
+        assert np.linalg.norm(r) <= 1e-10 * cf["lmax"]
+
+
+def test_deflate_normal_modes_small():
+    cf = setup((2, 2, 2, 4), 0.7, 4, 0.02, 80)
+    ctx = make_ctx(cf)
+    V = oracle.volume(cf["dims"])
+    A = dense(lambda v: oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], v,
+                                              cf["ev"], cf["eta"]), V)
+    mu = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
+    nev = 6
+    ctx.deflate(1, nev, 1e-9)
+    vals, vecs = ctx.get_eigenpairs(1)
+    assert np.allclose(np.sort(vals), mu[:nev], atol=1e-8 * mu[-1])
+    for i in range(nev):
+        r = A @ vecs[i] - vals[i] * vecs[i]
+        assert np.linalg.norm(r) <= 1e-8 * mu[-1]
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_cg_config1(cfg1, inner):
+    """Config 1: CG on D_ov^dag D_ov x = b to 1e-10 (true FP64 residual by the oracle)."""
+    cf = cfg1
+    ctx = make_ctx(cf)
+    b = synth.gaussian_spinor(cf["dims"], 2)
+    x = torch.empty_like(dev(b))
+    info = ctx.cg_solve(dev(b), x, mass=0.0, tol=1e-10, max_iter=2000, inner_prec=inner)
+    xs = host(x)
+    Ax = oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], xs, cf["ev"],
+                               cf["eta"])
+    res = rel(Ax, b)
+    print(f"cg config1 inner={inner}: iters {info['iterations']} updates {info['reliable_updates']} res {res:.2e}")
+    assert res <= 1e-10
+    assert info["true_residual"][0] <= 1e-10
+
+
+def test_deflated_cg_fewer_iterations(cfg1):
+    cf = cfg1
+    ctx = make_ctx(cf)
+    b = synth.gaussian_spinor(cf["dims"], 3, nrhs=2)
+    x = torch.empty_like(dev(b))
+    plain = ctx.cg_solve(dev(b), x, mass=0.02, tol=1e-10, max_iter=2000, inner_prec="f32")
+    ctx.deflate(1, 16, 1e-6)
+    defl = ctx.cg_solve(dev(b), x, mass=0.02, tol=1e-10, max_iter=2000, inner_prec="f32")
+    xs = host(x)
+    for r in range(2):
+        Ax = oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.02, cf["lmax"], cf["eps"], cf["c"], xs[r],
+                                   cf["ev"], cf["eta"])
+        assert rel(Ax, b[r]) <= 1e-10
+    print("cg iterations plain", plain["iterations"], "deflated", defl["iterations"])
+    assert defl["iterations"] < plain["iterations"]
+
+
+def test_cg_matches_oracle_solution():
+    cf = setup((2, 2, 2, 4), 0.5, 6, 0.02, 80)
+    ctx = make_ctx(cf)
+    b = synth.gaussian_spinor(cf["dims"], 7)
+    x = torch.empty_like(dev(b))
+    ctx.cg_solve(dev(b), x, mass=0.05, tol=1e-12, max_iter=3000)
+    xo, it, res = oracle.cg(cf["dims"], ABC, cf["U"], RHO, 0.05, cf["lmax"], cf["eps"], cf["c"], b, tol=1e-12,
+                            max_iter=3000, evals=cf["ev"], evecs=cf["eta"])
+    assert res <= 1e-12
+    # both solutions satisfy the same system to 1e-12; their difference is bounded by kappa * 1e-12
+    assert rel(host(x), xo) < 1e-8
