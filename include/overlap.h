@@ -136,6 +136,29 @@ int ov_get_eigenpairs(ov_ctx* ctx, int which, int* nev, double* vals, void* vecs
 int ov_cg_solve(ov_ctx* ctx, const void* b, void* x, int nrhs, double mass, double tol, int max_iter,
                 int precond, int inner_prec, ov_solve_info* info, void* stream);
 
+/* ---- learned preconditioner (no counterpart in the paper; used by
+ * ov_cg_solve with precond = 1).  M = L2 L1, each layer
+ *   y_c(n) = sum_{c'} sum_{p=0..8} W[p][c][c'] (T_p x_{c'})(n),
+ * T_0 = 1, T_{1+2mu} x(n) = U_mu(n) x(n+mu), T_{2+2mu} x(n) = U_mu(n-mu)^dag x(n-mu)
+ * (the parallel transporters of Eq. 2 without spin projectors), W a complex
+ * 4x4 spin matrix; channels 1 -> 16 -> 1.  Weights as 9216 doubles
+ * (interleaved re, im): layer 1 W[9][16][1][4][4], then layer 2 W[9][1][16][4][4]. */
+/* Record (residual, error) pairs from nsolves deflated mixed-precision CG
+ * solves of random sources on this context (mass `mass`), then run `steps`
+ * Adam steps (learning rate lr) on sum_k |M r_k - e_k|^2 / |e_k|^2.
+ * *final_loss (may be NULL) receives the mean loss per pair. */
+int ov_net_train(ov_ctx* ctx, int nsolves, int steps, double lr, double mass, double* final_loss, void* stream);
+int ov_net_set_weights(ov_ctx* ctx, const double* w, int n /* 9216 */);
+int ov_net_get_weights(ov_ctx* ctx, double* w, int n /* 9216 */);
+/* out = M in (canonical fields, host or device), computed in FP32. */
+int ov_net_apply(ov_ctx* ctx, const void* in, void* out, int nrhs, void* stream);
+/* loss = sum_k |M r_k - e_k|^2 / |e_k|^2 over npairs (<= 16) canonical fields
+ * and its gradient (9216 doubles, d/dRe W + i d/dIm W; may be NULL). */
+int ov_net_loss_grad(ov_ctx* ctx, const void* r, const void* e, int npairs, double* loss, double* grad,
+                     void* stream);
+/* Number of training pairs recorded by the last ov_net_train. */
+int ov_net_pairs(const ov_ctx* ctx);
+
 /* ---- internal-layout fields: an even/odd field kept on the device in one
  * storage precision, for chaining operators without repacking. ---- */
 int ov_field_create(ov_ctx* ctx, int nrhs, int prec, ov_field** f);
@@ -151,6 +174,14 @@ int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass
 
 /* Device bytes held by the context (gauge, eigenpairs, workspaces). */
 long long ov_device_bytes(const ov_ctx* ctx);
+/* Number of dslash kernel launches issued through this context so far
+ * (instrumentation: an overlap application costs 2n+1, Sec. V). */
+long long ov_dslash_count(const ov_ctx* ctx);
+/* Capture each overlap / D^dag D application in a CUDA graph on first use
+ * and replay it afterwards (enable = 1, the default; needs a non-NULL
+ * stream).  Graphs are dropped whenever the polynomial, the eigenpairs or
+ * a workspace pointer changes. */
+int ov_set_graphs(ov_ctx* ctx, int enable);
 /* Launch shape of the dslash for (prec, nrhs): block = bx sites x by rhs.
  * ov_tune_dslash times the candidates on `stream` and keeps the fastest. */
 int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by);

@@ -58,6 +58,12 @@ _SIGS = {
     "ov_set_eigenpairs": (_I, [_P, _I, _I, _P, _P, _P]),
     "ov_get_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P]),
     "ov_cg_solve": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
+    "ov_net_train": (_I, [_P, _I, _I, _D, _D, ctypes.POINTER(_D), _P]),
+    "ov_net_set_weights": (_I, [_P, _P, _I]),
+    "ov_net_get_weights": (_I, [_P, _P, _I]),
+    "ov_net_apply": (_I, [_P, _P, _P, _I, _P]),
+    "ov_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D), _P, _P]),
+    "ov_net_pairs": (_I, [_P]),
     "ov_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
     "ov_field_destroy": (_I, [_P]),
     "ov_field_import": (_I, [_P, _P, _P, _P]),
@@ -65,6 +71,8 @@ _SIGS = {
     "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
     "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
+    "ov_dslash_count": (ctypes.c_longlong, [_P]),
+    "ov_set_graphs": (_I, [_P, _I]),
     "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I]),
     "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
@@ -254,6 +262,38 @@ class Context:
             self._check(st)
         return info.as_dict() | {"status": st}
 
+    # -- learned preconditioner ---------------------------------------------------------
+    NET_DOUBLES = 9216
+
+    def net_train(self, nsolves=4, steps=100, lr=1e-2, mass=0.0, stream=None):
+        loss = _D()
+        self._check(self.lib.ov_net_train(self.h, int(nsolves), int(steps), float(lr), float(mass),
+                                          ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def net_weights(self):
+        w = np.empty(self.NET_DOUBLES)
+        self._check(self.lib.ov_net_get_weights(self.h, _ptr(w), self.NET_DOUBLES))
+        return w.view(np.complex128)
+
+    def net_set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.complex128)).view(np.float64)
+        self._check(self.lib.ov_net_set_weights(self.h, _ptr(w), self.NET_DOUBLES))
+
+    def net_apply(self, x, out, stream=None):
+        self._check(self.lib.ov_net_apply(self.h, _ptr(x), _ptr(out), self._nrhs(x), _stream(stream)))
+        return out
+
+    def net_loss_grad(self, r, e, stream=None):
+        loss = _D()
+        g = np.empty(self.NET_DOUBLES)
+        self._check(self.lib.ov_net_loss_grad(self.h, _ptr(r), _ptr(e), self._nrhs(r), ctypes.byref(loss), _ptr(g),
+                                              _stream(stream)))
+        return loss.value, g.view(np.complex128)
+
+    def net_pairs(self):
+        return int(self.lib.ov_net_pairs(self.h))
+
     def field(self, nrhs, prec):
         return Field(self, nrhs, prec)
 
@@ -265,6 +305,12 @@ class Context:
 
     def device_bytes(self):
         return int(self.lib.ov_device_bytes(self.h))
+
+    def dslash_count(self):
+        return int(self.lib.ov_dslash_count(self.h))
+
+    def set_graphs(self, enable):
+        self._check(self.lib.ov_set_graphs(self.h, int(bool(enable))))
 
     def set_dslash_shape(self, prec, nrhs, bx, by):
         self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by)))

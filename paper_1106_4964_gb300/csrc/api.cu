@@ -89,6 +89,7 @@ int ws_field(ov_ctx* c, int slot, int prec, int nrhs, FieldDesc* f)
 int ensure_partials(ov_ctx* c, size_t bytes)
 {
     if (bytes <= c->partials_bytes) return OV_OK;
+    graphs_clear(c);  // captured graphs hold the old pointer
     // the old buffer may still be read by queued kernels: wait before freeing
     if (c->partials) {
         cudaDeviceSynchronize();
@@ -364,18 +365,65 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
     return OV_OK;
 }
 
+void graphs_clear(ov_ctx* c)
+{
+    if (c->graphs.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+    c->graphs.clear();
+}
+
+// Run `body` (a fixed sequence of kernel launches on st) through a captured
+// CUDA graph: the first call for a key runs eagerly (allocating any
+// workspace) and then captures the same sequence; later calls replay it.
+template <typename F>
+static int with_graph(ov_ctx* c, int kind, const FieldDesc& in, const FieldDesc& out, double mass, int g5,
+                      cudaStream_t st, F body)
+{
+    if (!c->use_graphs || st == nullptr) return body();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return body();
+    auto key = std::make_tuple(kind, (const void*)in.data, (const void*)out.data, in.prec, in.nrhs, mass, g5);
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+        OV_CUDA(c, cudaGraphLaunch(it->second.first, st));
+        c->dslash_launches += it->second.second;
+        return OV_OK;
+    }
+    OV_TRY(body());
+    const long long before = c->dslash_launches;
+    OV_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int s = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    const long long n = c->dslash_launches - before;
+    c->dslash_launches = before;
+    if (s != OV_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s != OV_OK ? s : set_err(c, OV_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(c, OV_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    c->graphs[key] = {ex, n};
+    return OV_OK;
+}
+
 int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
 {
-    return overlap_apply_g5(c, in, out, mass, 0, st);
+    return with_graph(c, 0, in, out, mass, 0, st, [&]() { return overlap_apply_g5(c, in, out, mass, 0, st); });
 }
 
 int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
 {
     FieldDesc u;
     OV_TRY(ws_field(c, WS_AUX0, in.prec, in.nrhs, &u));
-    OV_TRY(overlap_apply_g5(c, in, u, mass, 1, st));   // u = g5 D in
-    OV_TRY(overlap_apply_g5(c, u, out, mass, 1, st));  // out = g5 D g5 D in = D^dag D in
-    return OV_OK;
+    return with_graph(c, 1, in, out, mass, 0, st, [&]() {
+        OV_TRY(overlap_apply_g5(c, in, u, mass, 1, st));  // u = g5 D in
+        return overlap_apply_g5(c, u, out, mass, 1, st);  // out = g5 D g5 D in = D^dag D in
+    });
 }
 
 // Chebyshev-interpolant coefficients of x^{-1/2} on [eps, 1] at the n+1
@@ -449,6 +497,7 @@ int ov_destroy(ov_ctx* c)
 {
     if (!c) return OV_EINVAL;
     cudaDeviceSynchronize();
+    graphs_clear(c);
     net_free(c);
     for (int p = 0; p < 4; ++p)
         if (c->gauge[p]) dev_free(c, c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p));
@@ -498,6 +547,7 @@ int ov_set_gauge(ov_ctx* c, const void* U, void* stream)
                        (double)e_unit, (double)e_row);
     }
     c->have_gauge = true;
+    graphs_clear(c);
     // eigenpairs of a previous gauge field no longer apply
     for (auto& e : c->eig) {
         for (auto& f : e.vec) field_free(c, &f);
@@ -558,6 +608,7 @@ int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambd
     if (!(eps > 0.0 && eps < 1.0)) return set_err(c, OV_EINVAL, "eps = %g outside (0, 1)", eps);
     if (degree < 0 || degree > 100000) return set_err(c, OV_EINVAL, "degree = %d out of range", degree);
     if (!(rho > 0.0 && rho < 2.0)) return set_err(c, OV_EINVAL, "rho = %g outside (0, 2)", rho);
+    graphs_clear(c);
     c->rho = rho;
     c->eps = eps;
     c->degree = degree;
@@ -593,6 +644,7 @@ int ov_set_eigenpairs(ov_ctx* c, int which, int nev, const double* vals, const v
     cudaStream_t st = (cudaStream_t)stream;
     EigSet& E = c->eig[which];
     OV_CUDA(c, cudaStreamSynchronize(st));
+    graphs_clear(c);
     for (auto& f : E.vec) field_free(c, &f);
     if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
     E.d_sign = nullptr;
@@ -756,6 +808,16 @@ int ov_overlap_field(ov_ctx* c, const ov_field* in, ov_field* out, double mass, 
 }
 
 long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
+
+long long ov_dslash_count(const ov_ctx* c) { return c ? c->dslash_launches : -1; }
+
+int ov_set_graphs(ov_ctx* c, int enable)
+{
+    if (!c) return OV_EINVAL;
+    graphs_clear(c);
+    c->use_graphs = enable != 0;
+    return OV_OK;
+}
 
 int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by)
 {

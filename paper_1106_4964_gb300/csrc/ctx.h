@@ -77,6 +77,12 @@ struct ov_ctx {
 
     ov::NetState* net = nullptr;
 
+    // captured CUDA graphs of whole operator applications:
+    // key (kind, in, out, prec, nrhs, mass, g5) -> (executable graph, dslash launches inside)
+    std::map<std::tuple<int, const void*, const void*, int, int, double, int>, std::pair<cudaGraphExec_t, long long>>
+        graphs;
+    bool use_graphs = true;
+
     // instrumentation: number of dslash launches issued through this context
     long long dslash_launches = 0;
 
@@ -100,6 +106,7 @@ int set_err(ov_ctx* c, int code, const char* fmt, ...);
     } while (0)
 
 int dev_alloc(ov_ctx* c, void** p, size_t bytes);
+void graphs_clear(ov_ctx* c);
 void dev_free(ov_ctx* c, void* p, size_t bytes);
 int field_alloc(ov_ctx* c, int prec, int nrhs, FieldDesc* f);
 void field_free(ov_ctx* c, FieldDesc* f);

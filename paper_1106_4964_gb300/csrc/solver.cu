@@ -273,154 +273,131 @@ int estimate_lambda_max(ov_ctx* c, int steps, double* lmax, cudaStream_t st)
     return OV_OK;
 }
 
-// Thick-restart Lanczos on F = T_K(Y(A)) (largest eigenvalues of F <-> smallest of A), then
-// Rayleigh-Ritz with the operator R (H_w for which = 0, A for which = 1).
-int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
+namespace {
+
+// v <- P_chi v = (v + chi gamma5 v) / 2 (chi = +-1); nothing for chi = 0
+int project_chiral(ov_ctx* c, const FieldDesc& v, int chi, cudaStream_t st)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    const long long N = 24LL * c->g.Vh;
-    if (nev >= N / 2) return set_err(c, OV_EINVAL, "nev = %d too large for a lattice of dimension %lld", nev, N);
-    int m = std::max((5 * nev) / 2, nev + 20);
-    m = (int)std::min<long long>(m, N - 1);
-    const int kkeep = std::min(m - 1, nev + (m - nev) / 3);
+    if (!chi) return OV_OK;
+    FieldDesc xs[2] = {v, v};
+    double2 h[2] = {make_double2(0.5, 0), make_double2(0.5 * chi, 0)};
+    return lincomb(c, v, 2, xs, h, nullptr, 2, nullptr, st);
+}
+
+struct LanczosWork {
+    FieldDesc basis, rot, Z, zero, w, tmp[3];
+};
+
+// Thick-restart Lanczos for the nev smallest eigenvalues of the Hermitian A on the
+// chirality-chi subspace (chi = 0: whole space; +-1: gamma5 = chi, enforced after
+// every operator application), accelerated by the Chebyshev filter T_K(Y(A)) on
+// [acut, bmax] whose cutoff comes from an unfiltered Lanczos run (its j-th Ritz value
+// bounds the j-th eigenvalue from above).  Converged Ritz vectors are refined by
+// Rayleigh-Ritz with R; the result is accepted when max_i |R eta_i - lam_i eta_i| <=
+// tol * rscale.  Vectors go to `out` (nev fields), values (sorted by |lam|) to vals.
+int trlan(ov_ctx* c, const OpFn& A, const OpFn& R, int K, double bmax, int nev, int m, int kkeep, double tol,
+          double rscale, int chi, unsigned long long seed, LanczosWork& W, std::vector<double>& vals,
+          const FieldDesc& out, double* maxres_out, cudaStream_t st)
+{
     int status = OV_OK;
-    // precision of the operator: FP64 for the H_w modes; for D^dag D modes FP64 unless tol is loose
-    const int oprec = (which == 1 && tol >= 1e-7) ? P_F32 : P_F64;
-
-    FieldDesc basis{}, rot{}, zero{}, w{}, tmp[3] = {}, ta{}, tb{}, tsa{}, tsb{};
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(st);
-        field_free(c, &basis);
-        field_free(c, &rot);
+    const FieldDesc& basis = W.basis;
+    OpFn Ac = [&](const FieldDesc& in, const FieldDesc& o) -> int {
+        OV_TRY(A(in, o));
+        return project_chiral(c, o, chi, st);
     };
-    OV_TRY(field_alloc(c, P_F64, m + 1, &basis));
-    if ((status = field_alloc(c, P_F64, std::max(kkeep, 2 * nev) + 1, &rot)) != OV_OK) {
-        cleanup();
-        return status;
-    }
-#define DF_TRY(x)                   \
-    do {                            \
-        int s__ = (x);              \
-        if (s__ != OV_OK) {         \
-            cleanup();              \
-            return s__;             \
-        }                           \
-    } while (0)
-    DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &zero));
-    DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &w));
-    DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
-    DF_TRY(ws_field(c, WS_B0, P_F64, 1, &tmp[0]));
-    DF_TRY(ws_field(c, WS_B1, P_F64, 1, &tmp[1]));
-    DF_TRY(ws_field(c, WS_B2, P_F64, 1, &tmp[2]));
-    DF_TRY(ws_field(c, WS_T, P_F64, 1, &tb));
-    if (oprec != P_F64) {
-        DF_TRY(ws_field(c, WS_CG_RS, oprec, 1, &tsa));
-        DF_TRY(ws_field(c, WS_CG_QS, oprec, 1, &tsb));
-    }
-    OV_CUDA(c, cudaMemsetAsync(zero.data, 0, zero.rhs_bytes() * 16, st));
-
-    // A = H_w^2 (which = 0) or D(0)^dag D(0) (which = 1); R = H_w or A
-    OpFn A, Rop;
-    double bmax;
-    if (which == 0) {
-        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-            return dslash_apply(c, ta, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
-        };
-        Rop = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            return dslash_apply(c, in, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
-        };
-        double lm = c->lmax;
-        if (!(lm > 0)) {
-            DF_TRY(estimate_lambda_max(c, 50, &lm, st));
-            lm *= 1.01;
-        }
-        bmax = lm * lm;
-    } else {
-        // the stored H_w modes deflate the sign inside D; keep them
-        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            if (oprec == P_F64) return normal_apply(c, in, out, 0.0, st);
-            OV_TRY(convert(c, in, tsa, st));
-            OV_TRY(normal_apply(c, tsa, tsb, 0.0, st));
-            return convert(c, tsb, out, st);
-        };
-        Rop = A;
-        bmax = 4.0 * c->rho * c->rho * 1.01;
-    }
-    // cutoff a from an unfiltered Lanczos run: the j-th Ritz value bounds the j-th eigenvalue from above
+    // cutoff from an unfiltered run
     std::vector<double> ritz0;
-    const int m0 = std::min(m, (int)std::min<long long>(N - 1, std::max(2 * nev + 20, 40)));
-    DF_TRY(plain_lanczos(c, A, m0, basis, w, 777ull + which, ritz0, st));
+    {
+        const int m0 = std::min(m, std::max(2 * nev + 20, 40));
+        OV_CUDA(c, launch_fill_random(c->g, sub(basis, 0), seed + 101, st));
+        OV_TRY(project_chiral(c, sub(basis, 0), chi, st));
+        double nr = host_norm(c, sub(basis, 0), st, &status);
+        OV_TRY(status);
+        OV_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
+        std::vector<cd> T((size_t)m0 * m0, cd(0, 0));
+        int mm = m0;
+        for (int j = 0; j < m0; ++j) {
+            OV_TRY(Ac(sub(basis, j), W.w));
+            std::vector<cd> h;
+            OV_TRY(cgs2(c, basis, j + 1, W.w, h, st));
+            for (int i = 0; i <= j; ++i) {
+                T[(size_t)i * m0 + j] = h[i];
+                T[(size_t)j * m0 + i] = std::conj(h[i]);
+            }
+            double beta = host_norm(c, W.w, st, &status);
+            OV_TRY(status);
+            if (j + 1 < m0) {
+                if (beta < 1e-12 * std::abs(T[(size_t)j * m0 + j]) + 1e-300) {
+                    mm = j + 1;
+                    break;
+                }
+                OV_TRY(scale_into(c, W.w, sub(basis, j + 1), 1.0 / beta, st));
+            }
+        }
+        std::vector<cd> Tm((size_t)mm * mm), Zt;
+        for (int i = 0; i < mm; ++i)
+            for (int j = 0; j < mm; ++j) Tm[(size_t)i * mm + j] = T[(size_t)i * m0 + j];
+        herm_eig(mm, Tm, ritz0, Zt);
+    }
     const int jcut = std::min((int)ritz0.size() - 1, nev + std::max(4, nev / 2));
     double acut = ritz0[jcut];
     if (!(acut < bmax)) acut = 0.5 * bmax;
-    const int K = which == 0 ? 100 : 8;
-    OpFn F = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-        return cheb_filter(c, A, K, acut, bmax, in, out, tmp, st);
+    OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
+        OV_TRY(cheb_filter(c, Ac, K, acut, bmax, in, o, W.tmp, st));
+        return project_chiral(c, o, chi, st);
     };
 
-    // thick-restart Lanczos on F
-    DF_TRY(launch_fill_random(c->g, sub(basis, 0), 4242ull + which, st) == cudaSuccess ? OV_OK : OV_ECUDA);
+    OV_CUDA(c, launch_fill_random(c->g, sub(basis, 0), seed, st));
+    OV_TRY(project_chiral(c, sub(basis, 0), chi, st));
     {
         double nr = host_norm(c, sub(basis, 0), st, &status);
-        DF_TRY(status);
-        DF_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
+        OV_TRY(status);
+        OV_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
     }
     std::vector<cd> T((size_t)m * m, cd(0, 0));
     std::vector<double> theta;
     std::vector<cd> Y;
+    std::vector<int> order(m);
     int k = 0;
-    double tolF = 1e-2 * tol;
-    bool done = false;
-    int restarts = 0;
-    std::vector<int> order;
-    double maxres = 0;
-    for (restarts = 0; restarts < 60 && !done; ++restarts) {
+    double tolF = tol;
+    double maxres = 1e300;
+    for (int restart = 0; restart < 300; ++restart) {
         double beta = 0;
         for (int j = k; j < m; ++j) {
-            DF_TRY(F(sub(basis, j), w));
+            OV_TRY(F(sub(basis, j), W.w));
             std::vector<cd> h;
-            DF_TRY(cgs2(c, basis, j + 1, w, h, st));
+            OV_TRY(cgs2(c, basis, j + 1, W.w, h, st));
             for (int i = 0; i <= j; ++i) {
-                if (i < k && j < k) continue;
                 T[(size_t)i * m + j] = h[i];
                 T[(size_t)j * m + i] = std::conj(h[i]);
             }
             T[(size_t)j * m + j] = h[j].real();
-            beta = host_norm(c, w, st, &status);
-            DF_TRY(status);
+            beta = host_norm(c, W.w, st, &status);
+            OV_TRY(status);
             if (beta < 1e-300) beta = 1e-300;
-            DF_TRY(scale_into(c, w, sub(basis, j + 1), 1.0 / beta, st));
+            OV_TRY(scale_into(c, W.w, sub(basis, j + 1), 1.0 / beta, st));
         }
         std::vector<cd> Tc = T;
-        DF_TRY(OV_OK);
         herm_eig(m, Tc, theta, Y);
-        // descending order of theta (largest of F = smallest of A)
-        order.resize(m);
-        for (int i = 0; i < m; ++i) order[i] = m - 1 - i;
-        const double tmax = std::fabs(theta[order[0]]);
+        for (int i = 0; i < m; ++i) order[i] = m - 1 - i;  // largest of F first
         int nconv = 0;
         for (int i = 0; i < nev; ++i) {
-            double r = beta * std::abs(Y[(size_t)(m - 1) * m + order[i]]);
-            if (r <= tolF * std::max(std::fabs(theta[order[i]]), 1e-300 * tmax)) ++nconv;
+            const double r = beta * std::abs(Y[(size_t)(m - 1) * m + order[i]]);
+            if (r <= tolF * std::fabs(theta[order[i]])) ++nconv;
         }
         if (nconv == nev) {
-            // Rayleigh-Ritz with R in span of the nev leading Ritz vectors, and true residuals
+            // Rayleigh-Ritz with R in the span of the nev leading Ritz vectors (basis untouched)
             std::vector<cd> Yk((size_t)m * nev);
             for (int i = 0; i < m; ++i)
                 for (int j = 0; j < nev; ++j) Yk[(size_t)i * nev + j] = Y[(size_t)i * m + order[j]];
-            FieldDesc Z = sub(rot, 0, nev);
-            DF_TRY(rotate(c, basis, m, Yk, nev, nev, Z, zero, st));
-            FieldDesc RZ = sub(basis, 0, nev);  // basis is free now
-            for (int j = 0; j < nev; ++j) DF_TRY(Rop(sub(Z, j), sub(RZ, j)));
+            OV_TRY(rotate(c, basis, m, Yk, nev, nev, W.Z, W.zero, st));
             std::vector<cd> M((size_t)nev * nev);
-            for (int j0 = 0; j0 < nev; j0 += 16) {
-                int nr = std::min(16, nev - j0);
-                DF_TRY(block_dots(c, Z, nev, sub(RZ, j0, nr), st));
-                std::vector<double2> hh((size_t)nev * nr);
-                DF_TRY(to_host(c, c->dscal, hh.data(), hh.size() * sizeof(double2), st));
-                for (int i = 0; i < nev; ++i)
-                    for (int r = 0; r < nr; ++r) M[(size_t)i * nev + j0 + r] = cd(hh[(size_t)i * nr + r].x, hh[(size_t)i * nr + r].y);
+            for (int j = 0; j < nev; ++j) {
+                OV_TRY(R(sub(W.Z, j), W.w));
+                OV_TRY(block_dots(c, W.Z, nev, W.w, st));
+                std::vector<double2> hh(nev);
+                OV_TRY(to_host(c, c->dscal, hh.data(), nev * sizeof(double2), st));
+                for (int i = 0; i < nev; ++i) M[(size_t)i * nev + j] = cd(hh[i].x, hh[i].y);
             }
             for (int i = 0; i < nev; ++i)
                 for (int j = i; j < nev; ++j) {
@@ -431,7 +408,6 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
             std::vector<double> lam;
             std::vector<cd> S;
             herm_eig(nev, M, lam, S);
-            // order by |lambda| (which = 0) or lambda (which = 1, all >= 0)
             std::vector<int> o(nev);
             for (int i = 0; i < nev; ++i) o[i] = i;
             std::sort(o.begin(), o.end(), [&](int a, int b) { return std::fabs(lam[a]) < std::fabs(lam[b]); });
@@ -441,79 +417,174 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
                 lo[j] = lam[o[j]];
                 for (int i = 0; i < nev; ++i) So[(size_t)i * nev + j] = S[(size_t)i * nev + o[j]];
             }
-            FieldDesc eta = sub(basis, nev, nev), Reta = sub(rot, 0, nev);
-            DF_TRY(rotate(c, Z, nev, So, nev, nev, eta, zero, st));
-            DF_TRY(rotate(c, RZ, nev, So, nev, nev, Reta, zero, st));
-            // residuals |R eta - lam eta| / scale
-            const double scale = which == 0 ? std::sqrt(bmax) : bmax;
+            FieldDesc eta = sub(W.rot, 0, nev);
+            OV_TRY(rotate(c, W.Z, nev, So, nev, nev, eta, W.zero, st));
             maxres = 0;
             for (int j = 0; j < nev; ++j) {
-                FieldDesc xs[2] = {sub(Reta, j), sub(eta, j)};
+                OV_TRY(R(sub(eta, j), W.w));
+                FieldDesc xs[2] = {W.w, sub(eta, j)};
                 double2 h[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
-                DF_TRY(lincomb(c, w, 2, xs, h, nullptr, 0, nullptr, st));
-                double r = host_norm(c, w, st, &status);
-                DF_TRY(status);
-                maxres = std::max(maxres, r / scale);
+                OV_TRY(lincomb(c, W.w, 2, xs, h, nullptr, 0, nullptr, st));
+                const double r = host_norm(c, W.w, st, &status);
+                OV_TRY(status);
+                maxres = std::max(maxres, r / rscale);
             }
-            if (maxres <= tol || restarts >= 59 || tolF < 1e-15) {
-                // store
-                EigSet& E = c->eig[which];
-                for (auto& f : E.vec) field_free(c, &f);
-                if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
-                E.d_sign = nullptr;
-                E.nev = 0;
-                DF_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
-                OV_CUDA(c, cudaMemcpyAsync(E.vec[P_F64].data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice,
-                                           st));
-                E.vals = lo;
-                E.nev = nev;
-                std::vector<double> sg(nev);
-                for (int i = 0; i < nev; ++i) sg[i] = lo[i] > 0 ? 1.0 : (lo[i] < 0 ? -1.0 : 0.0);
-                void* p = nullptr;
-                DF_TRY(dev_alloc(c, &p, sizeof(double) * nev));
-                E.d_sign = (double*)p;
-                OV_CUDA(c, cudaMemcpyAsync(E.d_sign, sg.data(), sizeof(double) * nev, cudaMemcpyHostToDevice, st));
+            if (maxres <= tol) {
+                OV_CUDA(c, cudaMemcpyAsync(out.data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
                 OV_CUDA(c, cudaStreamSynchronize(st));
-                done = true;
-                break;
+                vals = lo;
+                *maxres_out = maxres;
+                return OV_OK;
             }
-            // not accurate enough: tighten and restart from the Ritz vectors
             tolF *= 1e-2;
-            // rebuild: basis[0..nev) = eta is not a Krylov relation of F; restart plainly from Z
-            // (put Z back into basis and restart the Krylov recurrence with k = 0 from Z_0 + ...)
-            OV_CUDA(c, cudaMemcpyAsync(basis.data, Z.data, Z.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
-            // start vector: sum of the Ritz vectors (keeps all wanted directions)
-            {
-                std::vector<cd> ones((size_t)nev, cd(1.0, 0.0));
-                DF_TRY(rotate(c, sub(basis, 0, nev), nev, ones, 1, 1, sub(rot, 0), zero, st));
-                double nr = host_norm(c, sub(rot, 0), st, &status);
-                DF_TRY(status);
-                DF_TRY(scale_into(c, sub(rot, 0), sub(basis, 0), 1.0 / nr, st));
-            }
-            std::fill(T.begin(), T.end(), cd(0, 0));
-            k = 0;
-            continue;
+            if (tolF < 1e-16) break;
         }
-        // thick restart: keep the kkeep leading Ritz vectors
+        // thick restart with the kkeep leading Ritz vectors
         std::vector<cd> Yk((size_t)m * kkeep);
         for (int i = 0; i < m; ++i)
             for (int j = 0; j < kkeep; ++j) Yk[(size_t)i * kkeep + j] = Y[(size_t)i * m + order[j]];
-        DF_TRY(rotate(c, basis, m, Yk, kkeep, kkeep, rot, zero, st));
-        OV_CUDA(c, cudaMemcpyAsync(basis.data, rot.data, rot.rhs_bytes() * kkeep, cudaMemcpyDeviceToDevice, st));
+        OV_TRY(rotate(c, basis, m, Yk, kkeep, kkeep, W.rot, W.zero, st));
+        OV_CUDA(c, cudaMemcpyAsync(basis.data, W.rot.data, W.rot.rhs_bytes() * kkeep, cudaMemcpyDeviceToDevice, st));
         OV_CUDA(c, cudaMemcpyAsync(sub(basis, kkeep).data, sub(basis, m).data, basis.rhs_bytes(),
                                    cudaMemcpyDeviceToDevice, st));
         std::fill(T.begin(), T.end(), cd(0, 0));
         for (int i = 0; i < kkeep; ++i) T[(size_t)i * m + i] = theta[order[i]];
         k = kkeep;
     }
+    *maxres_out = maxres;
+    return set_err(c, OV_ENOTCONV, "Lanczos: max relative eigen-residual %.3e > tol %.3e", maxres, tol);
+}
+
+int store_eigs(ov_ctx* c, int which, const FieldDesc& vecs, const std::vector<int>& pick,
+               const std::vector<double>& vals, cudaStream_t st)
+{
+    EigSet& E = c->eig[which];
+    graphs_clear(c);
+    for (auto& f : E.vec) field_free(c, &f);
+    if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
+    E.d_sign = nullptr;
+    E.nev = 0;
+    E.vals.clear();
+    const int nev = (int)pick.size();
+    OV_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
+    std::vector<double> sg(nev);
+    for (int i = 0; i < nev; ++i) {
+        OV_CUDA(c, cudaMemcpyAsync(sub(E.vec[P_F64], i).data, sub(vecs, pick[i]).data, vecs.rhs_bytes(),
+                                   cudaMemcpyDeviceToDevice, st));
+        E.vals.push_back(vals[pick[i]]);
+        sg[i] = vals[pick[i]] > 0 ? 1.0 : (vals[pick[i]] < 0 ? -1.0 : 0.0);
+    }
+    void* p = nullptr;
+    OV_TRY(dev_alloc(c, &p, sizeof(double) * nev));
+    E.d_sign = (double*)p;
+    OV_CUDA(c, cudaMemcpyAsync(E.d_sign, sg.data(), sizeof(double) * nev, cudaMemcpyHostToDevice, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    E.nev = nev;
+    return OV_OK;
+}
+
+}  // namespace
+
+// which = 0: nev smallest-|lambda| eigenpairs of H_w (Lanczos on T_100(Y(H_w^2)), Rayleigh-Ritz with H_w).
+// which = 1: nev smallest eigenpairs of D(0)^dag D(0).  It commutes with gamma5 and its eigenvalues
+//            are doubly degenerate across the two chiral sectors (d and d* of D share |d|^2), which a
+//            single-vector Lanczos cannot resolve, so each sector is solved on its own (the chiral
+//            structure Sec. V uses) and the lowest nev of the union are kept.
+int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
+{
+    const long long N = 24LL * c->g.Vh;  // complex dimension 12 V
+    const int nsec = which == 0 ? 1 : 2;
+    const long long dim = which == 0 ? N : N / 2;
+    const int ns = which == 0 ? nev : std::min<long long>(nev / 2 + 4, nev);
+    if (ns >= dim / 2) return set_err(c, OV_EINVAL, "nev = %d too large for a lattice of dimension %lld", nev, N);
+    int m = std::max((5 * ns) / 2, ns + 20);
+    m = (int)std::min<long long>(m, dim - 1);
+    const int kkeep = std::min(m - 1, ns + (m - ns) / 3);
+    const int oprec = (which == 1 && tol >= 1e-7) ? P_F32 : P_F64;
+
+    LanczosWork W{};
+    FieldDesc outv{}, tsa{}, tsb{}, ta{};
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        field_free(c, &W.basis);
+        field_free(c, &W.rot);
+        field_free(c, &W.Z);
+        field_free(c, &outv);
+    };
+#define DF_TRY(x)           \
+    do {                    \
+        int s__ = (x);      \
+        if (s__ != OV_OK) { \
+            cleanup();      \
+            return s__;     \
+        }                   \
+    } while (0)
+    DF_TRY(field_alloc(c, P_F64, m + 1, &W.basis));
+    DF_TRY(field_alloc(c, P_F64, std::max(kkeep, ns), &W.rot));
+    DF_TRY(field_alloc(c, P_F64, ns, &W.Z));
+    DF_TRY(field_alloc(c, P_F64, nsec * ns, &outv));
+    DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &W.zero));
+    DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &W.w));
+    DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
+    DF_TRY(ws_field(c, WS_B0, P_F64, 1, &W.tmp[0]));
+    DF_TRY(ws_field(c, WS_B1, P_F64, 1, &W.tmp[1]));
+    DF_TRY(ws_field(c, WS_B2, P_F64, 1, &W.tmp[2]));
+    if (oprec != P_F64) {
+        DF_TRY(ws_field(c, WS_CG_RS, oprec, 1, &tsa));
+        DF_TRY(ws_field(c, WS_CG_QS, oprec, 1, &tsb));
+    }
+    OV_CUDA(c, cudaMemsetAsync(W.zero.data, 0, W.zero.rhs_bytes() * 16, st));
+
+    OpFn A, R;
+    double bmax, rscale;
+    int K;
+    if (which == 0) {
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return dslash_apply(c, ta, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
+        R = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            return dslash_apply(c, in, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
+        double lm = c->lmax;
+        if (!(lm > 0)) {
+            DF_TRY(estimate_lambda_max(c, 50, &lm, st));
+            lm *= 1.01;
+        }
+        bmax = lm * lm;
+        rscale = lm;
+        K = 100;
+    } else {
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            if (oprec == P_F64) return normal_apply(c, in, out, 0.0, st);
+            OV_TRY(convert(c, in, tsa, st));
+            OV_TRY(normal_apply(c, tsa, tsb, 0.0, st));
+            return convert(c, tsb, out, st);
+        };
+        R = A;
+        bmax = 4.0 * c->rho * c->rho * 1.01;
+        rscale = bmax;
+        K = 8;
+    }
+    std::vector<double> allv;
+    double worst = 0;
+    for (int s = 0; s < nsec; ++s) {
+        const int chi = which == 0 ? 0 : (s == 0 ? +1 : -1);
+        std::vector<double> v;
+        double mr = 0;
+        DF_TRY(trlan(c, A, R, K, bmax, ns, m, kkeep, tol, rscale, chi, 4242ull + 17 * which + s, W, v,
+                     sub(outv, s * ns, ns), &mr, st));
+        allv.insert(allv.end(), v.begin(), v.end());
+        worst = std::max(worst, mr);
+    }
+    std::vector<int> pick(allv.size());
+    for (size_t i = 0; i < pick.size(); ++i) pick[i] = (int)i;
+    std::stable_sort(pick.begin(), pick.end(), [&](int a, int b) { return std::fabs(allv[a]) < std::fabs(allv[b]); });
+    pick.resize(nev);
+    DF_TRY(store_eigs(c, which, outv, pick, allv, st));
     cleanup();
 #undef DF_TRY
-    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    (void)secs;
-    if (!done) return set_err(c, OV_ENOTCONV, "deflate(which=%d): not converged after %d restarts", which, restarts);
-    if (maxres > tol)
-        return set_err(c, OV_ENOTCONV, "deflate(which=%d): max relative eigen-residual %.3e > tol %.3e", which, maxres,
-                       tol);
+    (void)worst;
     return OV_OK;
 }
 
@@ -522,6 +593,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
 // ---------------------------------------------------------------------------
 int net_apply_precond(ov_ctx* c, const FieldDesc& r, const FieldDesc& z, cudaStream_t st);
 bool net_ready(const ov_ctx* c);
+int net_record_pair(ov_ctx* c, const FieldDesc& r64, const FieldDesc& x64, cudaStream_t st);
 
 int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
             int inner_prec, ov_solve_info* info, cudaStream_t st)
@@ -618,7 +690,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, doub
         }
         OV_TRY(project(xi64, r));
         ++updates;
-        return OV_OK;
+        return net_record_pair(c, r, x, st);
     };
     auto sloppy_norms = [&](const FieldDesc& v, std::vector<double>& out) -> int {
         OV_TRY(norm2(c, v, (double*)ddt, st));

@@ -31,7 +31,10 @@ def test_lambda_max_estimate(cfg1):
     ctx.set_gauge(dev(cfg1["U"]))
     ctx.set_sign_poly(RHO, 0.05, 10, 0.0)
     lm = ctx.get_sign_poly()["lambda_max"]
-    assert abs(lm / cfg1["lmax"] - 1) < 1e-6
+    top = cfg1["lmax"] / 1.01  # largest |eigenvalue| of H_w (dense)
+    # 50 Lanczos steps bound the top of the spectrum from below; the 1.01 margin must cover it
+    assert top <= lm <= 1.01 * top * (1 + 1e-12)
+    assert abs(lm / cfg1["lmax"] - 1) < 1e-3
 
 
 def test_deflate_hw_modes(cfg1):
