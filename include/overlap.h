@@ -171,6 +171,11 @@ int ov_field_export(ov_ctx* ctx, const ov_field* f, void* canonical, void* strea
 int ov_dslash_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double m, int gamma5, void* stream);
 /* out = D(m) in on internal fields (precision of the fields), in != out. */
 int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass, void* stream);
+/* Scalar products x_r^dag y_r of every right-hand side r (Sec. III: the
+ * global scalar product), accumulated in FP64 whatever the storage precision
+ * and reduced in a fixed order (bitwise reproducible).  out: 2 * nrhs doubles
+ * (re, im per rhs), host or device.  x and y: same precision and nrhs. */
+int ov_field_dot(ov_ctx* ctx, const ov_field* x, const ov_field* y, double* out, void* stream);
 
 /* Device bytes held by the context (gauge, eigenpairs, workspaces). */
 long long ov_device_bytes(const ov_ctx* ctx);
@@ -182,6 +187,15 @@ long long ov_dslash_count(const ov_ctx* ctx);
  * stream).  Graphs are dropped whenever the polynomial, the eigenpairs or
  * a workspace pointer changes. */
 int ov_set_graphs(ov_ctx* ctx, int enable);
+/* Solver tunables:
+ *   "reliable_delta" (0.1): ov_cg_solve recomputes the FP64 true residual when
+ *                    the inner-precision residual has dropped by this factor;
+ *   "filter_hw" (100): Chebyshev filter degree on H_w^2 in ov_deflate(0) (Sec. V: T_100);
+ *   "filter_dd" (8):  filter degree on D^dag D in ov_deflate(1);
+ *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks FP64 when
+ *                    tol < 1e-7 and FP32 otherwise (Gram-Schmidt and
+ *                    Rayleigh-Ritz stay FP64), or an ov_prec value. */
+int ov_set_option(ov_ctx* ctx, const char* name, double value);
 /* Launch shape of the dslash for (prec, nrhs): block = bx sites x by rhs.
  * ov_tune_dslash times the candidates on `stream` and keeps the fastest. */
 int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by);

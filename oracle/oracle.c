@@ -440,13 +440,13 @@ void or_overlap_normal(const int *d, const double *bc, const cplx *U, double rho
 /* deflated CG on D(m)^dagger D(m), Eq. (9) for the normal equations   */
 /* ------------------------------------------------------------------ */
 /* Solves A x = b, A = D(m)^dag D(m), to ||b - A x|| / ||b|| <= tol.
- * Deflation with nev2 eigenpairs (mu_i, xi_i) of A: the low part is solved
- * exactly, x_l = sum_i xi_i (xi_i^dag b) / mu_i (pairs with mu_i <=
- * zero_tol * mu_max are excluded: exact zero modes, pseudo-inverse), and CG
- * runs on the orthogonal complement with the residual projected by
- * P_perp = 1 - sum_i xi_i xi_i^dag after every update.  When the CG
- * residual meets tol, the true residual b - A x is recomputed; if it does
- * not meet tol the solve restarts from x with that residual.
+ * Deflation with nev2 eigenpairs (mu_i, xi_i) of A: every cycle forms the
+ * true residual r = b - A x and solves its low part exactly,
+ * x += sum_i xi_i (xi_i^dag r) / mu_i (pairs with mu_i <= zero_tol * mu_max
+ * are excluded: exact zero modes, pseudo-inverse); CG then runs on the
+ * orthogonal complement with the residual projected by
+ * P_perp = 1 - sum_i xi_i xi_i^dag after every update, until the CG
+ * residual meets tol; the next cycle checks the true residual.
  * Returns the number of CG iterations (negative if max_iter was reached);
  * *true_res gets the final ||b - A x|| / ||b||. */
 int or_cg(const int *d, const double *bc, const cplx *U, double rho, double mass, double lmax,
@@ -465,28 +465,28 @@ int or_cg(const int *d, const double *bc, const cplx *U, double rho, double mass
     double bnorm = sqrt(vnorm2(N, b));
     int iters = 0;
 
-    /* x = x_l (low-mode part, exact) */
     memset(x, 0, sizeof(cplx) * N);
-    for (int i = 0; i < nev2; ++i) {
-        if (mu[i] <= zero_tol * mu_max) continue;
-        const cplx *e = xi + (long)i * N;
-        cplx pr = vdot(N, e, b) / mu[i];
-        for (long k = 0; k < N; ++k) x[k] += pr * e[k];
-    }
     double rel = 1.0;
     for (int cycle = 0; cycle < 20 && iters < max_iter; ++cycle) {
-        /* r = P_perp (b - A x) */
+        /* r = b - A x */
         ddag_d(&a, rho, mass, x, q, t);
         for (long k = 0; k < N; ++k) r[k] = b[k] - q[k];
         rel = sqrt(vnorm2(N, r)) / bnorm;
         if (rel <= tol) break;
+        /* low-mode part solved exactly on the current residual (Eq. 9):
+           x += sum_i xi_i (xi_i^dag r) / mu_i, r <- P_perp r.  In the first cycle r = b
+           and this is the deflated initial guess; later cycles remove what is left of
+           the low-mode error when the xi_i are only approximate eigenvectors. */
         for (int i = 0; i < nev2; ++i) {
             const cplx *e = xi + (long)i * N;
             cplx pr = vdot(N, e, r);
+            if (mu[i] > zero_tol * mu_max)
+                for (long k = 0; k < N; ++k) x[k] += (pr / mu[i]) * e[k];
             for (long k = 0; k < N; ++k) r[k] -= pr * e[k];
         }
         memcpy(p, r, sizeof(cplx) * N);
         double rr = vnorm2(N, r);
+        if (sqrt(rr) / bnorm <= tol) continue; /* the low-mode solve was enough */
         while (iters < max_iter) {
             ddag_d(&a, rho, mass, p, q, t);
             double pq = creal(vdot(N, p, q));

@@ -70,9 +70,11 @@ _SIGS = {
     "ov_field_export": (_I, [_P, _P, _P, _P]),
     "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
     "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
+    "ov_field_dot": (_I, [_P, _P, _P, _P, _P]),
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
     "ov_dslash_count": (ctypes.c_longlong, [_P]),
     "ov_set_graphs": (_I, [_P, _I]),
+    "ov_set_option": (_I, [_P, ctypes.c_char_p, _D]),
     "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I]),
     "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
@@ -303,6 +305,11 @@ class Context:
     def overlap_field(self, fin: Field, fout: Field, mass=0.0, stream=None):
         self._check(self.lib.ov_overlap_field(self.h, fin.h, fout.h, float(mass), _stream(stream)))
 
+    def field_dot(self, x: Field, y: Field, stream=None):
+        out = np.empty(2 * x.nrhs)
+        self._check(self.lib.ov_field_dot(self.h, x.h, y.h, _ptr(out), _stream(stream)))
+        return out.view(np.complex128)
+
     def device_bytes(self):
         return int(self.lib.ov_device_bytes(self.h))
 
@@ -311,6 +318,9 @@ class Context:
 
     def set_graphs(self, enable):
         self._check(self.lib.ov_set_graphs(self.h, int(bool(enable))))
+
+    def set_option(self, name, value):
+        self._check(self.lib.ov_set_option(self.h, name.encode(), float(value)))
 
     def set_dslash_shape(self, prec, nrhs, bx, by):
         self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by)))

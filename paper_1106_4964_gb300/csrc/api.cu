@@ -807,9 +807,49 @@ int ov_overlap_field(ov_ctx* c, const ov_field* in, ov_field* out, double mass, 
     return overlap_apply(c, in->d, out->d, mass, (cudaStream_t)stream);
 }
 
+int ov_field_dot(ov_ctx* c, const ov_field* x, const ov_field* y, double* out, void* stream)
+{
+    if (!c || !x || !y || !out) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    if (x->d.prec != y->d.prec || x->d.nrhs != y->d.nrhs)
+        return set_err(c, OV_EINVAL, "fields differ in precision or nrhs");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dev = nullptr;
+    if (is_device_ptr(out)) {
+        dev = out;
+    } else {
+        if (x->d.nrhs * 2 > 1024) return set_err(c, OV_EINVAL, "too many right-hand sides");
+        dev = c->dscal + DSCAL_DOT;
+    }
+    OV_TRY(dot(c, x->d, y->d, (double2*)dev, st));
+    if (dev != out) {
+        OV_CUDA(c, cudaMemcpyAsync(out, dev, sizeof(double) * 2 * x->d.nrhs, cudaMemcpyDeviceToHost, st));
+        OV_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return OV_OK;
+}
+
 long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
 
 long long ov_dslash_count(const ov_ctx* c) { return c ? c->dslash_launches : -1; }
+
+int ov_set_option(ov_ctx* c, const char* name, double value)
+{
+    if (!c || !name) return c ? set_err(c, OV_EINVAL, "null option name") : OV_EINVAL;
+    const std::string n(name);
+    if (n == "reliable_delta") {
+        if (!(value > 0 && value < 1)) return set_err(c, OV_EINVAL, "reliable_delta must lie in (0, 1)");
+        c->reliable_delta = value;
+    } else if (n == "filter_hw" || n == "filter_dd") {
+        if (value < 0 || value > 10000) return set_err(c, OV_EINVAL, "filter degree out of range");
+        (n == "filter_hw" ? c->filter_hw : c->filter_dd) = (int)value;
+    } else if (n == "eig_prec") {
+        if (value < -1 || value > 3) return set_err(c, OV_EINVAL, "eig_prec must be -1 or an ov_prec");
+        c->eig_prec = (int)value;
+    } else {
+        return set_err(c, OV_EINVAL, "unknown option '%s'", name);
+    }
+    return OV_OK;
+}
 
 int ov_set_graphs(ov_ctx* c, int enable)
 {

@@ -33,7 +33,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
-    WS_LZ_W, WS_LZ_T, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
+    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
 
@@ -85,6 +85,12 @@ struct ov_ctx {
 
     // instrumentation: number of dslash launches issued through this context
     long long dslash_launches = 0;
+
+    // solver options (ov_set_option)
+    double reliable_delta = 0.1;  // FP64 true residual when the sloppy residual drops by this factor
+    int filter_hw = 100;          // Chebyshev filter degree on H_w^2 (deflate which = 0)
+    int filter_dd = 8;            // Chebyshev filter degree on D^dag D (deflate which = 1)
+    int eig_prec = -1;            // operator precision inside deflate: -1 automatic, else ov_prec
 
     std::string err;
 };

@@ -141,3 +141,24 @@ def test_full_size_sampled_sites(big, prec):
     sites = np.concatenate([[0, V - 1, V // 2], rng.integers(0, V, 253)])
     ref = oracle.dslash_sites(dims, ABC, U, -RHO, psi, sites)
     assert rel(got[sites], ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6), ("f16", 2e-3)])
+def test_field_dot(prec, tol):
+    """FP64-accumulated scalar products of internal fields (Sec. III) against numpy."""
+    from paper_1106_4964_gb300 import Context
+
+    dims = (6, 4, 4, 6)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(synth.unit_gauge(dims)))
+    x = synth.gaussian_spinor(dims, 31, nrhs=3)
+    y = synth.gaussian_spinor(dims, 32, nrhs=3)
+    fx, fy = ctx.field(3, prec), ctx.field(3, prec)
+    fx.load(dev(x))
+    fy.load(dev(y))
+    got = ctx.field_dot(fx, fy)
+    for r in range(3):
+        ref = np.vdot(x[r], y[r])
+        assert abs(got[r] - ref) <= tol * np.linalg.norm(x[r]) * np.linalg.norm(y[r])
+    # bitwise reproducible
+    assert np.array_equal(got, ctx.field_dot(fx, fy))

@@ -249,3 +249,23 @@ def test_cg_deflated_guess_is_exact_in_span(dense_overlap):
     x, it, res = oracle.cg(dims, ABC, U, RHO, 0.0, lmax, eps, c, b, tol=1e-10, max_iter=50,
                            evals=ev, evecs=eta, mu=mu[:8], xi=xi[:, :8].T.copy())
     assert it == 0 and res < 1e-10
+
+
+def test_cg_with_approximate_eigenvectors(dense_overlap):
+    """Deflation with eigenvectors perturbed at 1e-5 still reaches the dense solution: the
+    low part is re-solved on every cycle's true residual (Eq. 9 applied to the residual)."""
+    dims, U, D, (lmax, eps, c, ev, eta) = dense_overlap
+    V = oracle.volume(dims)
+    m = 0.05
+    Dm = (RHO - m / 2) * (D / RHO) + m * np.eye(12 * V)
+    A = Dm.conj().T @ Dm
+    b = synth.gaussian_spinor(dims, 8)[0].reshape(-1)
+    mu, xi = np.linalg.eigh(0.5 * (A + A.conj().T))
+    rng = np.random.default_rng(5)
+    xp = xi[:, :10] + 1e-5 * (rng.standard_normal((12 * V, 10)) + 1j * rng.standard_normal((12 * V, 10)))
+    xp, _ = np.linalg.qr(xp)
+    mup = np.real(np.einsum("ki,kl,li->i", xp.conj(), A, xp))
+    x, it, res = oracle.cg(dims, ABC, U, RHO, m, lmax, eps, c, b, tol=1e-12, max_iter=800, evals=ev, evecs=eta,
+                           mu=mup, xi=xp.T.copy())
+    assert it > 0 and res <= 1e-12
+    assert rel(x, np.linalg.solve(A, b)) < 1e-9
