@@ -176,6 +176,21 @@ int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass
  * and reduced in a fixed order (bitwise reproducible).  out: 2 * nrhs doubles
  * (re, im per rhs), host or device.  x and y: same precision and nrhs. */
 int ov_field_dot(ov_ctx* ctx, const ov_field* x, const ov_field* y, double* out, void* stream);
+/* The paper has no counterpart: the same scalar products as ov_field_dot for
+ * callers that cannot allocate device memory when they call (for example
+ * while a CUDA graph is being captured in global mode, or under a memory
+ * manager that owns the whole device).  It never allocates: the partial sums
+ * live in one fixed 311 KB array of the library's device image, which every
+ * GPU that loads the library holds until the process exits.  Limits: up to
+ * 16 right-hand sides (the field maximum) and 1216 reduction blocks.  The
+ * first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and every call overwrites it completely, so
+ * calls that overlap on the GPU (other streams, other threads) race: order
+ * them.  The current device must be the fields' device.  out: 2 * nrhs
+ * doubles, host or device.  Errors are returned as status codes only
+ * (ov_last_error is not updated, since setting its text could allocate). */
+int ov_field_dot_noalloc(const ov_field* x, const ov_field* y, double* out, void* stream);
 
 /* Device bytes held by the context (gauge, eigenpairs, workspaces). */
 long long ov_device_bytes(const ov_ctx* ctx);

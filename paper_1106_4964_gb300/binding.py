@@ -71,6 +71,7 @@ _SIGS = {
     "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
     "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
     "ov_field_dot": (_I, [_P, _P, _P, _P, _P]),
+    "ov_field_dot_noalloc": (_I, [_P, _P, _P, _P]),
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
     "ov_dslash_count": (ctypes.c_longlong, [_P]),
     "ov_set_graphs": (_I, [_P, _I]),
@@ -309,6 +310,15 @@ class Context:
         out = np.empty(2 * x.nrhs)
         self._check(self.lib.ov_field_dot(self.h, x.h, y.h, _ptr(out), _stream(stream)))
         return out.view(np.complex128)
+
+    def field_dot_noalloc(self, x: Field, y: Field, out=None, stream=None):
+        """ov_field_dot_noalloc: out is a host numpy array (default) or a device tensor of 2*nrhs doubles."""
+        if out is None:
+            out = np.empty(2 * x.nrhs)
+        st = self.lib.ov_field_dot_noalloc(x.h, y.h, _ptr(out), _stream(stream))
+        if st != 0:
+            raise OverlapError(st, "ov_field_dot_noalloc failed")
+        return out.view(np.complex128) if isinstance(out, np.ndarray) else out
 
     def device_bytes(self):
         return int(self.lib.ov_device_bytes(self.h))
