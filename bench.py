@@ -156,7 +156,7 @@ def run_gpu(args):
     prec = "f32"
     fi, fo = ctx.field(1, prec), ctx.field(1, prec)
     fi.load(psi_dev)
-    bx, by = ctx.tune_dslash(prec, 1)
+    bx, by, var = ctx.tune_dslash(prec, 1)
     st = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.dslash_field(fi, fo, -RHO)
@@ -242,7 +242,7 @@ def run_gpu(args):
                                "per launch", "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: gauge 170 MB + spinors 2 x 85 MB per launch",
-                   "launch_shape": [bx, by], "launches_per_step": reps},
+                   "launch_shape": [bx, by], "variant": var, "launches_per_step": reps},
         "gflops": round(gflops * world, 1),
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind,
@@ -320,6 +320,201 @@ def run_reference(args):
         "gflops": round(FLOP_SITE * V / dt / 1e9, 3)}))
 
 
+# ---------------------------------------------------------------------------------------
+# further workloads (not run by default): the overlap application, the batched
+# propagator and the learned preconditioner.  Each prints one JSON line.
+# ---------------------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_overlap(args):
+    """Overlap application on 24^3 x 64 (rho 1.5): the lowest nev H_w modes deflated (Lanczos on
+    T_100(H_w^2), FP32 filter, FP64 Gram-Schmidt and Rayleigh-Ritz), degree-n Chebyshev on the rest,
+    eps = (0.99 |lambda_nev| / lambda_max)^2.  Times one application per precision (1 and 12 rhs)
+    and reports each precision's error against the FP64 application."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims) if args.dims else DIMS
+    V = int(np.prod(dims))
+    import synth
+
+    U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
+    ctx = ov.Context(dims, BC)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    t0 = time.perf_counter()
+    ctx.set_sign_poly(RHO, 0.05, args.degree, 0.0)
+    lmax = ctx.get_sign_poly()["lambda_max"]
+    t_lmax = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.deflate(0, args.nev, args.eig_tol)
+    torch.cuda.synchronize()
+    t_defl = time.perf_counter() - t0
+    vals, _ = ctx.get_eigenpairs(0)
+    eps = (0.99 * np.abs(vals).max() / lmax) ** 2
+    ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+    psi = torch.from_numpy(synth.gaussian_spinor(dims, seed=2, nrhs=1)).cuda()
+    psi12 = torch.from_numpy(synth.gaussian_spinor(dims, seed=3, nrhs=12)).cuda()
+    ref = None
+    res = {}
+    for prec in ("f64", "f32", "f16", "bf16"):
+        for nrhs, src in ((1, psi), (12, psi12)):
+            if nrhs == 12 and prec == "f64" and not args.f64_r12:
+                continue
+            ctx.tune_dslash(prec, nrhs)
+            fi, fo = ctx.field(nrhs, prec), ctx.field(nrhs, prec)
+            fi.load(src)
+            ctx.overlap_field(fi, fo)  # graph capture
+            torch.cuda.synchronize()
+            n0 = ctx.dslash_count()
+            e0, e1 = _events(torch)
+            reps = 1 if prec == "f64" else args.reps
+            e0.record()
+            for _ in range(reps):
+                ctx.overlap_field(fi, fo)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            launches = (ctx.dslash_count() - n0) // reps
+            out = torch.empty_like(src)
+            fo.store(out)
+            if prec == "f64" and nrhs == 1:
+                ref = out.clone()
+            err = None
+            if nrhs == 1 and ref is not None:
+                err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+            res[f"{prec}_r{nrhs}"] = {"ms": round(ms, 3), "applications_per_s": round(1e3 * nrhs / ms, 3),
+                                      "dslash_launches": int(launches), "rel_err_vs_f64": err}
+            fi.close()
+            fo.close()
+    main = res["f32_r1"]
+    print(json.dumps({
+        "metric": "overlap applications/s", "value": main["applications_per_s"], "unit": "applications/s",
+        "n_gpus": 1, "steps": args.reps, "warmup": 1, "ms_per_step": main["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"overlap D(0) application, {dims[0]}^3x{dims[3]}, rho 1.5, {args.nev} deflated H_w "
+                               f"modes, degree {args.degree}", "lattice": list(dims), "eps": eps,
+                   "lambda_max": lmax},
+        "setup_s": {"lambda_max": round(t_lmax, 2), "deflate": round(t_defl, 2)},
+        "eigen": {"nev": int(len(vals)), "min_abs": float(np.abs(vals).min()), "max_abs": float(np.abs(vals).max())},
+        "precisions": res}))
+
+
+def run_propagator(args):
+    """Batched propagator: 12 spin-colour point sources at the origin, rho 1.5, the lowest nev H_w
+    modes deflated in the sign and the lowest nev_cg modes of D^dag D deflating the CG, mixed-precision
+    CG on D^dag D to 1e-10 with FP64 reliable updates, 12 rhs in one multi-RHS launch per dslash,
+    graph-captured operator applications, autotuned launch shape."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+    import synth
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims) if args.dims else (32, 32, 32, 64)
+    U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
+    ctx = ov.Context(dims, BC)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    ctx.set_option("reliable_delta", args.delta)
+    setup = {}
+    t0 = time.perf_counter()
+    ctx.set_sign_poly(RHO, 0.05, args.degree, 0.0)
+    lmax = ctx.get_sign_poly()["lambda_max"]
+    setup["lambda_max"] = time.perf_counter() - t0
+    eps = 0.05
+    if args.nev > 0:
+        t0 = time.perf_counter()
+        ctx.deflate(0, args.nev, args.eig_tol)
+        setup["deflate_hw"] = time.perf_counter() - t0
+        vals, _ = ctx.get_eigenpairs(0)
+        eps = (0.99 * np.abs(vals).max() / lmax) ** 2
+    ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+    if args.nev_cg > 0:
+        ctx.set_option("filter_dd", args.filter_dd)
+        t0 = time.perf_counter()
+        ctx.deflate(1, args.nev_cg, args.eig_tol)
+        setup["deflate_dd"] = time.perf_counter() - t0
+    b = torch.from_numpy(synth.point_sources(dims)).cuda()
+    for p in ("f32", "f16", "f64"):
+        ctx.tune_dslash(p, 12)
+    out = {}
+    for inner in args.inner.split(","):
+        x = torch.empty_like(b)
+        info = ctx.cg_solve(b, x, mass=args.mass, tol=1e-10, max_iter=args.max_iter, inner_prec=inner)
+        out[inner] = {"seconds": round(info["seconds"], 2), "iterations": info["iterations"],
+                      "reliable_updates": info["reliable_updates"],
+                      "max_true_residual": max(info["true_residual"]),
+                      "solves_per_s": round(12 / info["seconds"], 4)}
+    best = min(out.values(), key=lambda d: d["seconds"])
+    print(json.dumps({
+        "metric": "overlap propagator solves/s at res 1e-10", "value": best["solves_per_s"], "unit": "solves/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(1e3 * best["seconds"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed f32/f16 + f64",
+        "data": "synthetic",
+        "config": {"workload": f"12 point sources, {dims[0]}^3x{dims[3]}, rho 1.5, mass {args.mass}, "
+                               f"{args.nev} H_w modes + {args.nev_cg} D^dag D modes, degree {args.degree}",
+                   "lattice": list(dims), "eps": eps, "lambda_max": lmax},
+        "propagators_per_s": round(best["solves_per_s"] / 12, 5),
+        "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out}))
+
+
+def run_learned(args):
+    """Learned preconditioner: train on (residual, error) pairs of deflated CG solves on a small
+    lattice, move the weights to the large lattice, and compare flexible CG with plain deflated
+    CG on 12 sources (iterations and time to 1e-10)."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+    import synth
+
+    torch.cuda.set_device(0)
+    small = tuple(args.train_dims)
+    big = tuple(args.dims) if args.dims else (32, 32, 32, 64)
+    res = {}
+
+    def prepare(dims):
+        U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
+        ctx = ov.Context(dims, BC)
+        ctx.set_gauge(torch.from_numpy(U).cuda())
+        ctx.set_sign_poly(RHO, 0.05, args.degree, 0.0)
+        lmax = ctx.get_sign_poly()["lambda_max"]
+        eps = 0.05
+        if args.nev > 0:
+            ctx.deflate(0, args.nev, args.eig_tol)
+            vals, _ = ctx.get_eigenpairs(0)
+            eps = (0.99 * np.abs(vals).max() / lmax) ** 2
+        ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+        if args.nev_cg > 0:
+            ctx.set_option("filter_dd", args.filter_dd)
+            ctx.deflate(1, args.nev_cg, args.eig_tol)
+        return ctx
+
+    t0 = time.perf_counter()
+    cs = prepare(small)
+    loss = cs.net_train(nsolves=args.train_solves, steps=args.train_steps, lr=args.lr, mass=args.mass)
+    res["train"] = {"seconds": round(time.perf_counter() - t0, 1), "pairs": cs.net_pairs(), "loss_per_pair": loss}
+    w = cs.net_weights()
+    cs.close()
+    cb = prepare(big)
+    cb.net_set_weights(w)
+    b = torch.from_numpy(synth.point_sources(big)).cuda()
+    for name, pc in (("plain", 0), ("learned", 1)):
+        x = torch.empty_like(b)
+        info = cb.cg_solve(b, x, mass=args.mass, tol=1e-10, max_iter=args.max_iter, precond=pc, inner_prec="f32",
+                           check=False)
+        res[name] = {"seconds": round(info["seconds"], 2), "iterations": info["iterations"],
+                     "fallback": info["fallback"], "max_true_residual": max(info["true_residual"]),
+                     "status": info["status"]}
+    print(json.dumps({
+        "metric": "time to 1e-10, learned flexible CG vs plain deflated CG", "value": res["learned"]["seconds"],
+        "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * res["learned"]["seconds"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f64", "data": "synthetic",
+        "config": {"workload": f"train {small}, apply {big}, 12 point sources, mass {args.mass}"}, "results": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,11 +525,34 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default="dslash", choices=["dslash", "overlap", "propagator", "learned"])
+    ap.add_argument("--dims", type=int, nargs=4, default=None)
+    ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 32])
+    ap.add_argument("--degree", type=int, default=200)
+    ap.add_argument("--nev", type=int, default=100)
+    ap.add_argument("--nev-cg", type=int, default=100)
+    ap.add_argument("--filter-dd", type=int, default=8)
+    ap.add_argument("--eig-tol", type=float, default=1e-6)
+    ap.add_argument("--mass", type=float, default=0.0)
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--inner", default="f32")
+    ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--f64-r12", action="store_true")
+    ap.add_argument("--train-solves", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=100)
+    ap.add_argument("--lr", type=float, default=5e-3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "overlap":
+        run_overlap(args)
+    elif args.workload == "propagator":
+        run_propagator(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

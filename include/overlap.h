@@ -211,10 +211,12 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *                    tol < 1e-7 and FP32 otherwise (Gram-Schmidt and
  *                    Rayleigh-Ritz stay FP64), or an ov_prec value. */
 int ov_set_option(ov_ctx* ctx, const char* name, double value);
-/* Launch shape of the dslash for (prec, nrhs): block = bx sites x by rhs.
- * ov_tune_dslash times the candidates on `stream` and keeps the fastest. */
-int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by);
-int ov_tune_dslash(ov_ctx* ctx, int prec, int nrhs, int* bx, int* by, void* stream);
+/* Launch configuration of the dslash for (prec, nrhs): block = bx sites x by
+ * right-hand sides, and a register-budget variant (0: unbounded; 1, 2:
+ * registers capped so that more warps are resident).  ov_tune_dslash times
+ * every candidate on `stream` and keeps the fastest (the autotuner). */
+int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by, int variant);
+int ov_tune_dslash(ov_ctx* ctx, int prec, int nrhs, int* bx, int* by, int* variant, void* stream);
 
 #ifdef __cplusplus
 }

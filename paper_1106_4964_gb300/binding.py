@@ -76,8 +76,8 @@ _SIGS = {
     "ov_dslash_count": (ctypes.c_longlong, [_P]),
     "ov_set_graphs": (_I, [_P, _I]),
     "ov_set_option": (_I, [_P, ctypes.c_char_p, _D]),
-    "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I]),
-    "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
+    "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I, _I]),
+    "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
 
 
@@ -332,11 +332,11 @@ class Context:
     def set_option(self, name, value):
         self._check(self.lib.ov_set_option(self.h, name.encode(), float(value)))
 
-    def set_dslash_shape(self, prec, nrhs, bx, by):
-        self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by)))
+    def set_dslash_shape(self, prec, nrhs, bx, by, variant=0):
+        self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by), int(variant)))
 
     def tune_dslash(self, prec, nrhs, stream=None):
-        bx, by = _I(), _I()
+        bx, by, var = _I(), _I(), _I()
         self._check(self.lib.ov_tune_dslash(self.h, _prec(prec), int(nrhs), ctypes.byref(bx), ctypes.byref(by),
-                                            _stream(stream)))
-        return bx.value, by.value
+                                            ctypes.byref(var), _stream(stream)))
+        return bx.value, by.value, var.value

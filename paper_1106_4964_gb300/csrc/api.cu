@@ -173,12 +173,12 @@ int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out)
     return OV_OK;
 }
 
-static std::pair<int, int> default_shape(int prec, int nrhs)
+static std::tuple<int, int, int> default_shape(int prec, int nrhs)
 {
-    if (nrhs == 1) return {prec == P_F64 ? 64 : 128, 1};
+    if (nrhs == 1) return {prec == P_F64 ? 64 : 128, 1, 0};
     const int cap = prec == P_F64 ? 8 : 16;
     int by = nrhs > cap ? cap : nrhs;
-    return {32, by};
+    return {32, by, 0};
 }
 
 int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a, double b, int g5_core, int g5_out,
@@ -204,8 +204,8 @@ int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a,
     A.g5_core = g5_core;
     A.g5_out = g5_out;
     auto it = c->shape.find({in.prec, in.nrhs});
-    std::pair<int, int> sh = it != c->shape.end() ? it->second : default_shape(in.prec, in.nrhs);
-    OV_CUDA(c, launch_dslash(A, in.prec, gprec, ny, sh.first, sh.second, st));
+    std::tuple<int, int, int> sh = it != c->shape.end() ? it->second : default_shape(in.prec, in.nrhs);
+    OV_CUDA(c, launch_dslash(A, in.prec, gprec, ny, std::get<0>(sh), std::get<1>(sh), std::get<2>(sh), st));
     c->dslash_launches++;
     return OV_OK;
 }
@@ -859,17 +859,18 @@ int ov_set_graphs(ov_ctx* c, int enable)
     return OV_OK;
 }
 
-int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by)
+int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int variant)
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
-    if (bx < 1 || by < 1 || bx * by > (prec == P_F64 ? 256 : 512) || bx % 32)
-        return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
-    c->shape[{prec, nrhs}] = {bx, by};
+    if (variant < 0 || variant >= DSLASH_VARIANTS) return set_err(c, OV_EINVAL, "bad variant %d", variant);
+    const int maxt = variant == 0 ? (prec == P_F64 ? 256 : 512) : 256;
+    if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
+    c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
 }
 
-int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, void* stream)
+int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant, void* stream)
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
@@ -881,24 +882,28 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, void* stream
     OV_TRY(ws_field(c, WS_OUT, prec, nrhs, &fo));
     OV_CUDA(c, cudaMemsetAsync(fi.data, 0, data_bytes(prec, nrhs, c->g.Vh), st));
     if (fi.norm) OV_CUDA(c, cudaMemsetAsync(fi.norm, 0, norm_bytes(prec, nrhs, c->g.Vh), st));
-    std::vector<std::pair<int, int>> cand;
-    for (int x : {32, 64, 128, 256})
-        for (int y = 1; y <= nrhs && y <= 16; ++y) {
-            if (nrhs % y && y != nrhs) continue;
-            if (x * y > (prec == P_F64 ? 256 : 512) || x * y < 64) continue;
-            cand.push_back({x, y});
-        }
+    // candidates: block = x sites by y right-hand sides, times the register-budget variants
+    std::vector<std::tuple<int, int, int>> cand;
+    for (int v = 0; v < DSLASH_VARIANTS; ++v) {
+        const int maxt = v == 0 ? (prec == P_F64 ? 256 : 512) : 256;
+        for (int x : {32, 64, 128, 256})
+            for (int y = 1; y <= nrhs && y <= 16; ++y) {
+                if (nrhs % y && y != nrhs) continue;
+                if (x * y > maxt || x * y < 64) continue;
+                cand.push_back(std::make_tuple(x, y, v));
+            }
+    }
     if (cand.empty()) cand.push_back(default_shape(prec, nrhs));
     cudaEvent_t e0, e1;
     OV_CUDA(c, cudaEventCreate(&e0));
     OV_CUDA(c, cudaEventCreate(&e1));
     float best = 1e30f;
-    std::pair<int, int> bsh = cand[0];
+    std::tuple<int, int, int> bsh = cand[0];
     for (auto sh : cand) {
         c->shape[{prec, nrhs}] = sh;
         OV_TRY(dslash_apply(c, fi, fo, 4.0, -0.5, 0, 0, 0, nullptr, nullptr, st));
         OV_CUDA(c, cudaEventRecord(e0, st));
-        for (int i = 0; i < 5; ++i) OV_TRY(dslash_apply(c, fi, fo, 4.0, -0.5, 0, 0, 0, nullptr, nullptr, st));
+        for (int i = 0; i < 10; ++i) OV_TRY(dslash_apply(c, fi, fo, 4.0, -0.5, 0, 0, 0, nullptr, nullptr, st));
         OV_CUDA(c, cudaEventRecord(e1, st));
         OV_CUDA(c, cudaEventSynchronize(e1));
         float ms = 0;
@@ -911,8 +916,9 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, void* stream
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->shape[{prec, nrhs}] = bsh;
-    if (bx) *bx = bsh.first;
-    if (by) *by = bsh.second;
+    if (bx) *bx = std::get<0>(bsh);
+    if (by) *by = std::get<1>(bsh);
+    if (variant) *variant = std::get<2>(bsh);
     return OV_OK;
 }
 

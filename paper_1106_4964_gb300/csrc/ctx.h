@@ -33,7 +33,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
-    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
+    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
 
@@ -73,7 +73,7 @@ struct ov_ctx {
     size_t stage_bytes[2] = {0, 0};
     unsigned* derr = nullptr;
 
-    std::map<std::pair<int, int>, std::pair<int, int>> shape;  // (prec, nrhs) -> (bx, by)
+    std::map<std::pair<int, int>, std::tuple<int, int, int>> shape;  // (prec, nrhs) -> (bx, by, variant)
 
     ov::NetState* net = nullptr;
 

@@ -149,8 +149,17 @@ __device__ __forceinline__ void hop(const DslashArgs& A, const char* in_q, const
     accumulate<MU, S, Real>(acc, chi);
 }
 
-template <int SP, int GP, int NY>
-__global__ void __launch_bounds__(SP == P_F64 ? 256 : 512) dslash_kernel(DslashArgs A)
+// Register-budget variants chosen by the autotuner: VAR 0 lets the compiler
+// use what it wants (low occupancy, long latency chains), VAR 1 and 2 cap
+// the registers so that more warps are resident to hide load latency.
+template <int SP, int VAR>
+struct Bounds {
+    static constexpr int maxt = VAR == 0 ? (SP == P_F64 ? 256 : 512) : 256;
+    static constexpr int minb = VAR == 0 ? 1 : (SP == P_F64 ? VAR + 1 : VAR + 2);
+};
+
+template <int SP, int GP, int NY, int VAR>
+__global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) dslash_kernel(DslashArgs A)
 {
     using Real = real_t<SP>;
     const int p = blockIdx.x & 1;
@@ -216,32 +225,44 @@ __global__ void __launch_bounds__(SP == P_F64 ? 256 : 512) dslash_kernel(DslashA
     store_spinor<SP, Real>(A.out + off, A.out_n ? A.out_n + noff : nullptr, g.Vh, s, o);
 }
 
-template <int SP, int GP>
-cudaError_t launch_ny(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
+template <int SP, int GP, int VAR>
+cudaError_t launch_var(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
 {
+    if ((int)(block.x * block.y) > Bounds<SP, VAR>::maxt) return cudaErrorInvalidValue;
     switch (ny) {
-    case 0: dslash_kernel<SP, GP, 0><<<grid, block, 0, st>>>(A); break;
-    case 1: dslash_kernel<SP, GP, 1><<<grid, block, 0, st>>>(A); break;
-    case 2: dslash_kernel<SP, GP, 2><<<grid, block, 0, st>>>(A); break;
-    case 3: dslash_kernel<SP, GP, 3><<<grid, block, 0, st>>>(A); break;
+    case 0: dslash_kernel<SP, GP, 0, VAR><<<grid, block, 0, st>>>(A); break;
+    case 1: dslash_kernel<SP, GP, 1, VAR><<<grid, block, 0, st>>>(A); break;
+    case 2: dslash_kernel<SP, GP, 2, VAR><<<grid, block, 0, st>>>(A); break;
+    case 3: dslash_kernel<SP, GP, 3, VAR><<<grid, block, 0, st>>>(A); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+template <int SP, int GP>
+cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 block, cudaStream_t st)
+{
+    switch (var) {
+    case 0: return launch_var<SP, GP, 0>(A, ny, grid, block, st);
+    case 1: return launch_var<SP, GP, 1>(A, ny, grid, block, st);
+    case 2: return launch_var<SP, GP, 2>(A, ny, grid, block, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
-cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, cudaStream_t st)
+cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st)
 {
     if (bx <= 0 || by <= 0 || bx * by > (sp == P_F64 ? 256 : 512)) return cudaErrorInvalidValue;
     dim3 block(bx, by);
     dim3 grid(2 * ((A.g.Vh + bx - 1) / bx), (A.nrhs + by - 1) / by);
-    if (sp == P_F64 && gp == P_F64) return launch_ny<P_F64, P_F64>(A, ny, grid, block, st);
-    if (sp == P_F32 && gp == P_F32) return launch_ny<P_F32, P_F32>(A, ny, grid, block, st);
-    if (sp == P_F16 && gp == P_F16) return launch_ny<P_F16, P_F16>(A, ny, grid, block, st);
-    if (sp == P_BF16 && gp == P_BF16) return launch_ny<P_BF16, P_BF16>(A, ny, grid, block, st);
-    if (sp == P_F32 && gp == P_F16) return launch_ny<P_F32, P_F16>(A, ny, grid, block, st);
-    if (sp == P_F32 && gp == P_BF16) return launch_ny<P_F32, P_BF16>(A, ny, grid, block, st);
+    if (sp == P_F64 && gp == P_F64) return launch_ny<P_F64, P_F64>(A, ny, var, grid, block, st);
+    if (sp == P_F32 && gp == P_F32) return launch_ny<P_F32, P_F32>(A, ny, var, grid, block, st);
+    if (sp == P_F16 && gp == P_F16) return launch_ny<P_F16, P_F16>(A, ny, var, grid, block, st);
+    if (sp == P_BF16 && gp == P_BF16) return launch_ny<P_BF16, P_BF16>(A, ny, var, grid, block, st);
+    if (sp == P_F32 && gp == P_F16) return launch_ny<P_F32, P_F16>(A, ny, var, grid, block, st);
+    if (sp == P_F32 && gp == P_BF16) return launch_ny<P_F32, P_BF16>(A, ny, var, grid, block, st);
     return cudaErrorInvalidValue;
 }
 

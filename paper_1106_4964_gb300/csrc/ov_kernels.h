@@ -23,7 +23,9 @@ struct DslashArgs {
     int nrhs;
     int g5_core, g5_out;
 };
-cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, cudaStream_t st);
+// var: register-budget variant (0 unbounded, 1 and 2 capped for occupancy)
+cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st);
+constexpr int DSLASH_VARIANTS = 3;
 
 // ---------------------------------------------------------------- layout conversion
 // canonical complex128 [nrhs][V][12] (device) <-> internal field

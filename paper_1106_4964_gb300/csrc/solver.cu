@@ -170,30 +170,50 @@ int scale_into(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double s, c
 using OpFn = std::function<int(const FieldDesc&, const FieldDesc&)>;
 
 // Chebyshev filter: out = T_K(Y) in, Y = (2 A - (a+b)) / (b-a), three-term recurrence
+// The recurrence runs in the precision of the work fields tmp[0..3] (A acts on
+// fields of that precision); in and out are converted once if they differ.
+// K = 0 gives the plain spectral flip F = b - A (largest of F = smallest of A).
 int cheb_filter(ov_ctx* c, const OpFn& A, int K, double a, double b, const FieldDesc& in, const FieldDesc& out,
-                FieldDesc tmp[3], cudaStream_t st)
+                FieldDesc tmp[4], cudaStream_t st)
 {
-    if (K == 0) return copy_field(c, in, out, st);
-    const double s1 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
-    // y1 = Y in
-    FieldDesc q = tmp[0];
-    OV_TRY(A(in, q));
-    FieldDesc prev = tmp[1], cur = tmp[2];
-    OV_TRY(copy_field(c, in, prev, st));
-    {
-        FieldDesc xs[2] = {q, in};
-        double2 h[2] = {make_double2(s1, 0), make_double2(s0, 0)};
-        OV_TRY(lincomb(c, K == 1 ? out : cur, 2, xs, h, nullptr, 0, nullptr, st));
+    const bool conv = tmp[0].prec != in.prec;
+    FieldDesc q = tmp[0], y_prev = tmp[1], y_cur = tmp[2];
+    FieldDesc x0 = in;
+    if (conv) {
+        x0 = tmp[3];
+        OV_TRY(convert(c, in, x0, st));
     }
-    if (K == 1) return OV_OK;
-    for (int j = 1; j < K; ++j) {
-        OV_TRY(A(cur, q));
-        FieldDesc dst = j == K - 1 ? out : prev;  // y_{j+1} overwrites y_{j-1}
-        FieldDesc xs[3] = {q, cur, prev};
-        double2 h[3] = {make_double2(2 * s1, 0), make_double2(2 * s0, 0), make_double2(-1, 0)};
-        OV_TRY(lincomb(c, dst, 3, xs, h, nullptr, 0, nullptr, st));
-        if (j < K - 1) std::swap(prev, cur);
+    FieldDesc last;
+    if (K == 0) {
+        OV_TRY(A(x0, q));
+        last = conv ? y_cur : out;
+        FieldDesc xs[2] = {x0, q};
+        double2 h[2] = {make_double2(b, 0), make_double2(-1, 0)};
+        OV_TRY(lincomb(c, last, 2, xs, h, nullptr, 0, nullptr, st));
+    } else {
+        const double s1 = 2.0 / (b - a), s0 = -(a + b) / (b - a);
+        OV_TRY(A(x0, q));  // y1 = Y y0
+        if (conv)
+            y_prev = x0;  // the converted input is a work field of its own
+        else
+            OV_TRY(copy_field(c, x0, y_prev, st));
+        last = (K == 1 && !conv) ? out : y_cur;
+        {
+            FieldDesc xs[2] = {q, x0};
+            double2 h[2] = {make_double2(s1, 0), make_double2(s0, 0)};
+            OV_TRY(lincomb(c, last, 2, xs, h, nullptr, 0, nullptr, st));
+        }
+        for (int j = 1; j < K; ++j) {
+            OV_TRY(A(y_cur, q));
+            FieldDesc dst = (j == K - 1 && !conv) ? out : y_prev;  // y_{j+1} overwrites y_{j-1}
+            FieldDesc xs[3] = {q, y_cur, y_prev};
+            double2 h[3] = {make_double2(2 * s1, 0), make_double2(2 * s0, 0), make_double2(-1, 0)};
+            OV_TRY(lincomb(c, dst, 3, xs, h, nullptr, 0, nullptr, st));
+            last = dst;
+            std::swap(y_prev, y_cur);
+        }
     }
+    if (conv) OV_TRY(convert(c, last, out, st));
     return OV_OK;
 }
 
@@ -285,7 +305,7 @@ int project_chiral(ov_ctx* c, const FieldDesc& v, int chi, cudaStream_t st)
 }
 
 struct LanczosWork {
-    FieldDesc basis, rot, Z, zero, w, tmp[3];
+    FieldDesc basis, rot, Z, zero, w, tmp[4];
 };
 
 // Thick-restart Lanczos for the nev smallest eigenvalues of the Hermitian A on the
@@ -295,14 +315,19 @@ struct LanczosWork {
 // bounds the j-th eigenvalue from above).  Converged Ritz vectors are refined by
 // Rayleigh-Ritz with R; the result is accepted when max_i |R eta_i - lam_i eta_i| <=
 // tol * rscale.  Vectors go to `out` (nev fields), values (sorted by |lam|) to vals.
-int trlan(ov_ctx* c, const OpFn& A, const OpFn& R, int K, double bmax, int nev, int m, int kkeep, double tol,
-          double rscale, int chi, unsigned long long seed, LanczosWork& W, std::vector<double>& vals,
+int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, double bmax, int nev, int m, int kkeep,
+          double tol, double rscale, int chi, unsigned long long seed, LanczosWork& W, std::vector<double>& vals,
           const FieldDesc& out, double* maxres_out, cudaStream_t st)
 {
     int status = OV_OK;
     const FieldDesc& basis = W.basis;
+    // A on FP64 fields (unfiltered run) and Awork on fields of the filter's work precision
     OpFn Ac = [&](const FieldDesc& in, const FieldDesc& o) -> int {
         OV_TRY(A(in, o));
+        return project_chiral(c, o, chi, st);
+    };
+    OpFn AcW = [&](const FieldDesc& in, const FieldDesc& o) -> int {
+        OV_TRY(Awork(in, o));
         return project_chiral(c, o, chi, st);
     };
     // cutoff from an unfiltered run
@@ -343,7 +368,7 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& R, int K, double bmax, int nev, 
     double acut = ritz0[jcut];
     if (!(acut < bmax)) acut = 0.5 * bmax;
     OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
-        OV_TRY(cheb_filter(c, Ac, K, acut, bmax, in, o, W.tmp, st));
+        OV_TRY(cheb_filter(c, AcW, K, acut, bmax, in, o, W.tmp, st));
         return project_chiral(c, o, chi, st);
     };
 
@@ -528,22 +553,29 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &W.zero));
     DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &W.w));
     DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
-    // filter temporaries: slots of their own (the Clenshaw buffers are used inside D^dag D)
-    DF_TRY(ws_field(c, WS_LZ_F0, P_F64, 1, &W.tmp[0]));
-    DF_TRY(ws_field(c, WS_LZ_F1, P_F64, 1, &W.tmp[1]));
-    DF_TRY(ws_field(c, WS_LZ_F2, P_F64, 1, &W.tmp[2]));
+    // filter temporaries in the operator's precision: slots of their own (the Clenshaw
+    // buffers are used inside D^dag D)
+    DF_TRY(ws_field(c, WS_LZ_F0, oprec, 1, &W.tmp[0]));
+    DF_TRY(ws_field(c, WS_LZ_F1, oprec, 1, &W.tmp[1]));
+    DF_TRY(ws_field(c, WS_LZ_F2, oprec, 1, &W.tmp[2]));
+    DF_TRY(ws_field(c, WS_LZ_F3, oprec, 1, &W.tmp[3]));
     if (oprec != P_F64) {
         DF_TRY(ws_field(c, WS_CG_RS, oprec, 1, &tsa));
         DF_TRY(ws_field(c, WS_CG_QS, oprec, 1, &tsb));
     }
     OV_CUDA(c, cudaMemsetAsync(W.zero.data, 0, W.zero.rhs_bytes() * 16, st));
 
-    OpFn A, R;
+    OpFn A, Awork, R;
     double bmax, rscale;
     int K;
     FieldDesc tsc{};
     if (oprec != P_F64) DF_TRY(ws_field(c, WS_LZ_T, oprec, 1, &tsc));
     if (which == 0) {
+        Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+            const FieldDesc& tmid = oprec == P_F64 ? ta : tsc;
+            OV_TRY(dslash_apply(c, in, tmid, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return dslash_apply(c, tmid, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+        };
         A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
             if (oprec == P_F64) {
                 OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
@@ -572,6 +604,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
             OV_TRY(normal_apply(c, tsa, tsb, 0.0, st));
             return convert(c, tsb, out, st);
         };
+        Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int { return normal_apply(c, in, out, 0.0, st); };
         R = A;
         bmax = 4.0 * c->rho * c->rho * 1.01;
         rscale = bmax;
@@ -583,7 +616,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         const int chi = which == 0 ? 0 : (s == 0 ? +1 : -1);
         std::vector<double> v;
         double mr = 0;
-        DF_TRY(trlan(c, A, R, K, bmax, ns, m, kkeep, tol, rscale, chi, 4242ull + 17 * which + s, W, v,
+        DF_TRY(trlan(c, A, Awork, R, K, bmax, ns, m, kkeep, tol, rscale, chi, 4242ull + 17 * which + s, W, v,
                      sub(outv, s * ns, ns), &mr, st));
         allv.insert(allv.end(), v.begin(), v.end());
         worst = std::max(worst, mr);
