@@ -403,6 +403,57 @@ def run_overlap(args):
         "precisions": res}))
 
 
+def run_project(args):
+    """Low-mode projection c = v^dag psi at 24^3 x 64 with nev seeded random unit vectors standing in
+    for eigenvectors (the contraction does not depend on their values): tensor cores (bf16 rows)
+    against the CUDA cores (FP32 rows), 1 and 12 right-hand sides."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+    import synth
+
+    torch.cuda.set_device(0)
+    dims = tuple(args.dims) if args.dims else DIMS
+    V = int(np.prod(dims))
+    ctx = ov.Context(dims, BC)
+    ctx.set_gauge(torch.from_numpy(synth.unit_gauge(dims)).cuda())
+    g = torch.Generator(device="cuda").manual_seed(7)
+    vecs = torch.randn((args.nev, V * 12), dtype=torch.complex128, device="cuda", generator=g)
+    vecs /= torch.linalg.vector_norm(vecs, dim=1, keepdim=True)
+    ctx.set_eigenpairs(1, np.ones(args.nev), vecs)
+    del vecs
+    torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    out = {}
+    for nrhs in (1, 12):
+        psi = torch.from_numpy(synth.gaussian_spinor(dims, seed=2, nrhs=nrhs)).cuda()
+        f = ctx.field(nrhs, "f32")
+        f.load(psi)
+        K = 24 * V
+        for engine, name in ((1, "tensor_cores_bf16"), (0, "cuda_cores_f32")):
+            ctx.project_lowmodes(1, f, engine=engine)
+            e0, e1 = _events(torch)
+            e0.record()
+            for _ in range(args.reps):
+                ctx.project_lowmodes(1, f, engine=engine)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            row_bytes = 2 if engine == 1 else 4
+            bytes_alg = args.nev * K * row_bytes + nrhs * K * 4
+            npad = ((2 * nrhs + 15) // 16) * 16
+            out[f"{name}_r{nrhs}"] = {"ms": round(ms, 4), "GBps": round(bytes_alg / ms / 1e6, 1),
+                                      "frac_hbm": round(bytes_alg / ms / 1e6 / hbm, 3),
+                                      "tensor_TFLOPps": round(2 * 128 * npad * K / ms / 1e9, 2) if engine else None}
+        f.close()
+    print(json.dumps({"metric": "low-mode projection GB/s", "value": out["tensor_cores_bf16_r12"]["GBps"],
+                      "unit": "GB/s", "n_gpus": 1, "steps": args.reps, "warmup": 1,
+                      "ms_per_step": out["tensor_cores_bf16_r12"]["ms"], "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32", "data": "synthetic",
+                      "config": {"workload": f"c = v^dag psi, {args.nev} vectors, {dims}", "lattice": list(dims)},
+                      "results": out}))
+
+
 def run_propagator(args):
     """Batched propagator: 12 spin-colour point sources at the origin, rho 1.5, the lowest nev H_w
     modes deflated in the sign and the lowest nev_cg modes of D^dag D deflating the CG, mixed-precision
@@ -441,7 +492,7 @@ def run_propagator(args):
     for p in ("f32", "f16", "f64"):
         ctx.tune_dslash(p, 12)
     out = {}
-    for inner in args.inner.split(","):
+    for inner in args.cg_inner.split(","):
         x = torch.empty_like(b)
         info = ctx.cg_solve(b, x, mass=args.mass, tol=1e-10, max_iter=args.max_iter, inner_prec=inner)
         out[inner] = {"seconds": round(info["seconds"], 2), "iterations": info["iterations"],
@@ -525,7 +576,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="dslash", choices=["dslash", "overlap", "propagator", "learned"])
+    ap.add_argument("--workload", default="dslash", choices=["dslash", "overlap", "propagator", "learned", "project"])
     ap.add_argument("--dims", type=int, nargs=4, default=None)
     ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 32])
     ap.add_argument("--degree", type=int, default=200)
@@ -535,7 +586,7 @@ def main():
     ap.add_argument("--eig-tol", type=float, default=1e-6)
     ap.add_argument("--mass", type=float, default=0.0)
     ap.add_argument("--delta", type=float, default=0.1)
-    ap.add_argument("--inner", default="f32")
+    ap.add_argument("--cg-inner", default="f32", help="inner precisions of the propagator CG, comma separated")
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64-r12", action="store_true")
@@ -553,6 +604,8 @@ def main():
         run_propagator(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "project":
+        run_project(args)
     else:
         run_gpu(args)
 

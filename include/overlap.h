@@ -171,6 +171,15 @@ int ov_field_export(ov_ctx* ctx, const ov_field* f, void* canonical, void* strea
 int ov_dslash_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double m, int gamma5, void* stream);
 /* out = D(m) in on internal fields (precision of the fields), in != out. */
 int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass, void* stream);
+/* Low-mode projection coefficients c[i][r] = v_i^dag psi_r of the stored
+ * eigenvectors (which = 0: H_w modes, Eqs. 6-7; which = 1: D^dag D modes,
+ * Eq. 9), out: 2 * nev * nrhs doubles (re, im; [i][r]), host or device.
+ * engine 0: CUDA cores in the field's precision (FP64 for an FP64 field);
+ * engine 1: tensor cores (tcgen05, bf16 operands, FP32 accumulation, FP64
+ * sum of the split-K partials), nev <= 128, which is what the 16-bit overlap
+ * uses (option "proj_tc").  Returns OV_ETIMEOUT if a bounded wait inside the
+ * tensor-core kernel gave up. */
+int ov_project_lowmodes(ov_ctx* ctx, int which, const ov_field* psi, int engine, double* out, void* stream);
 /* Scalar products x_r^dag y_r of every right-hand side r (Sec. III: the
  * global scalar product), accumulated in FP64 whatever the storage precision
  * and reduced in a fixed order (bitwise reproducible).  out: 2 * nrhs doubles
@@ -209,7 +218,9 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *   "filter_dd" (8):  filter degree on D^dag D in ov_deflate(1);
  *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks FP64 when
  *                    tol < 1e-7 and FP32 otherwise (Gram-Schmidt and
- *                    Rayleigh-Ritz stay FP64), or an ov_prec value. */
+ *                    Rayleigh-Ritz stay FP64), or an ov_prec value;
+ *   "proj_tc" (1):    16-bit overlap: compute eta^dag psi on the tensor cores
+ *                    (0: on the CUDA cores). */
 int ov_set_option(ov_ctx* ctx, const char* name, double value);
 /* Launch configuration of the dslash for (prec, nrhs): block = bx sites x by
  * right-hand sides, and a register-budget variant (0: unbounded; 1, 2:

@@ -71,6 +71,7 @@ _SIGS = {
     "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
     "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
     "ov_field_dot": (_I, [_P, _P, _P, _P, _P]),
+    "ov_project_lowmodes": (_I, [_P, _I, _P, _I, _P, _P]),
     "ov_field_dot_noalloc": (_I, [_P, _P, _P, _P]),
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
     "ov_dslash_count": (ctypes.c_longlong, [_P]),
@@ -305,6 +306,14 @@ class Context:
 
     def overlap_field(self, fin: Field, fout: Field, mass=0.0, stream=None):
         self._check(self.lib.ov_overlap_field(self.h, fin.h, fout.h, float(mass), _stream(stream)))
+
+    def project_lowmodes(self, which, psi: Field, engine=0, stream=None):
+        """c[i][r] = v_i^dag psi_r of the stored eigenvectors; engine 0 CUDA cores, 1 tensor cores."""
+        n = _I()
+        self._check(self.lib.ov_get_eigenpairs(self.h, int(which), ctypes.byref(n), None, None, _stream(stream)))
+        out = np.empty(2 * n.value * psi.nrhs)
+        self._check(self.lib.ov_project_lowmodes(self.h, int(which), psi.h, int(engine), _ptr(out), _stream(stream)))
+        return out.view(np.complex128).reshape(n.value, psi.nrhs)
 
     def field_dot(self, x: Field, y: Field, stream=None):
         out = np.empty(2 * x.nrhs)

@@ -301,8 +301,15 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
         OV_TRY(ensure_partials(c, nparts * ncoef * sizeof(double2)));
         if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "overlap: nev * nrhs = %zu too large", ncoef);
         double2* dcoef = (double2*)c->dscal;
-        OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
-        OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
+        // 16-bit storage: c = eta^dag psi as a bf16 tensor-core GEMM; otherwise on the CUDA cores
+        const bool tc = c->proj_tc && (P == P_F16 || P == P_BF16) && E.nev <= 128 && 2 * R <= 256 &&
+                        (48LL * c->g.Vh) % 64 == 0;
+        if (tc) {
+            OV_TRY(proj_dots_tc(c, 0, in, dcoef, st));
+        } else {
+            OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
+            OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
+        }
         OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));
         src = ph;
     }
@@ -363,6 +370,18 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
     double sy[2] = {rho + 0.5 * mass, rho - 0.5 * mass};
     OV_TRY(dslash_apply(c, *pin, out, kk * psc * aw, -0.5 * kk * psc, 0, g5_out, defl ? 2 : 1, y, sy, st));
     return OV_OK;
+}
+
+void eig_clear(ov_ctx* c, EigSet& E)
+{
+    for (auto& f : E.vec) field_free(c, &f);
+    if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
+    if (E.tc_rows) dev_free(c, E.tc_rows, E.tc_bytes);
+    E.d_sign = nullptr;
+    E.tc_rows = nullptr;
+    E.tc_bytes = 0;
+    E.nev = 0;
+    E.vals.clear();
 }
 
 void graphs_clear(ov_ctx* c)
@@ -501,12 +520,11 @@ int ov_destroy(ov_ctx* c)
     net_free(c);
     for (int p = 0; p < 4; ++p)
         if (c->gauge[p]) dev_free(c, c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p));
-    for (auto& e : c->eig) {
-        for (auto& f : e.vec) field_free(c, &f);
-        if (e.d_sign) dev_free(c, e.d_sign, sizeof(double) * e.nev);
-    }
+    for (auto& e : c->eig) eig_clear(c, e);
     for (auto& kv : c->ws) field_free(c, &kv.second);
     if (c->partials) dev_free(c, c->partials, c->partials_bytes);
+    if (c->tc_b) dev_free(c, c->tc_b, c->tc_b_bytes);
+    if (c->tc_err) dev_free(c, c->tc_err, sizeof(int));
     for (int i = 0; i < 2; ++i)
         if (c->stage[i]) dev_free(c, c->stage[i], c->stage_bytes[i]);
     dev_free(c, c->dscal, DSCAL_DOUBLES * sizeof(double));
@@ -549,13 +567,7 @@ int ov_set_gauge(ov_ctx* c, const void* U, void* stream)
     c->have_gauge = true;
     graphs_clear(c);
     // eigenpairs of a previous gauge field no longer apply
-    for (auto& e : c->eig) {
-        for (auto& f : e.vec) field_free(c, &f);
-        if (e.d_sign) dev_free(c, e.d_sign, sizeof(double) * e.nev);
-        e.d_sign = nullptr;
-        e.nev = 0;
-        e.vals.clear();
-    }
+    for (auto& e : c->eig) eig_clear(c, e);
     return OV_OK;
 }
 
@@ -645,11 +657,7 @@ int ov_set_eigenpairs(ov_ctx* c, int which, int nev, const double* vals, const v
     EigSet& E = c->eig[which];
     OV_CUDA(c, cudaStreamSynchronize(st));
     graphs_clear(c);
-    for (auto& f : E.vec) field_free(c, &f);
-    if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
-    E.d_sign = nullptr;
-    E.nev = 0;
-    E.vals.clear();
+    eig_clear(c, E);
     if (nev == 0) return OV_OK;
     OV_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
     const size_t one = (size_t)2 * c->g.Vh * 12 * 16;
@@ -828,6 +836,37 @@ int ov_field_dot(ov_ctx* c, const ov_field* x, const ov_field* y, double* out, v
     return OV_OK;
 }
 
+int ov_project_lowmodes(ov_ctx* c, int which, const ov_field* psi, int engine, double* out, void* stream)
+{
+    if (!c || !psi || !out) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    if (which != 0 && which != 1) return set_err(c, OV_EINVAL, "which = %d (0 or 1)", which);
+    EigSet& E = c->eig[which];
+    if (!E.nev) return set_err(c, OV_ESTATE, "no eigenpairs stored (which=%d)", which);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R = psi->d.nrhs;
+    const size_t ncoef = (size_t)E.nev * R;
+    if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "nev * nrhs = %zu too large", ncoef);
+    double2* dev = (double2*)c->dscal;
+    if (engine == 1) {
+        OV_TRY(proj_dots_tc(c, which, psi->d, dev, st));
+        OV_TRY(proj_tc_status(c, st));
+    } else if (engine == 0) {
+        FieldDesc eta;
+        const int pv = psi->d.prec == P_F64 ? P_F64 : (psi->d.prec == P_F32 ? P_F32 : psi->d.prec);
+        OV_TRY(eig_vectors(c, which, pv, st, &eta));
+        const int nblk = reduce_blocks(c->g);
+        const int nparts = nblk * proj_groups(R);
+        OV_TRY(ensure_partials(c, nparts * ncoef * sizeof(double2)));
+        OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, psi->d, (double2*)c->partials, nblk, st));
+        OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dev, st));
+    } else {
+        return set_err(c, OV_EINVAL, "engine = %d (0 CUDA cores, 1 tensor cores)", engine);
+    }
+    OV_CUDA(c, cudaMemcpyAsync(out, dev, ncoef * sizeof(double2), cudaMemcpyDefault, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    return OV_OK;
+}
+
 long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
 
 long long ov_dslash_count(const ov_ctx* c) { return c ? c->dslash_launches : -1; }
@@ -845,6 +884,9 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
     } else if (n == "eig_prec") {
         if (value < -1 || value > 3) return set_err(c, OV_EINVAL, "eig_prec must be -1 or an ov_prec");
         c->eig_prec = (int)value;
+    } else if (n == "proj_tc") {
+        graphs_clear(c);
+        c->proj_tc = value != 0;
     } else {
         return set_err(c, OV_EINVAL, "unknown option '%s'", name);
     }

@@ -42,6 +42,8 @@ struct EigSet {
     std::vector<double> vals;   // host copy
     FieldDesc vec[4] = {};      // per storage precision (F64 is the master copy)
     double* d_sign = nullptr;   // device sign(lam_i) (which = 0)
+    void* tc_rows = nullptr;    // bf16 rows of the tensor-core projection [nev][24V]
+    size_t tc_bytes = 0;
 };
 
 struct NetState;  // learned preconditioner (net.cu)
@@ -91,6 +93,12 @@ struct ov_ctx {
     int filter_hw = 100;          // Chebyshev filter degree on H_w^2 (deflate which = 0)
     int filter_dd = 8;            // Chebyshev filter degree on D^dag D (deflate which = 1)
     int eig_prec = -1;            // operator precision inside deflate: -1 automatic, else ov_prec
+    int proj_tc = 1;              // 16-bit overlap: low-mode projection on the tensor cores
+
+    // tensor-core projection buffers (proj_tc.cu)
+    void* tc_b = nullptr;
+    size_t tc_b_bytes = 0;
+    int* tc_err = nullptr;
 
     std::string err;
 };
@@ -146,5 +154,11 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st);
 int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
             int inner_prec, ov_solve_info* info, cudaStream_t st);
 void net_free(ov_ctx* c);
+
+// eigenpairs
+void eig_clear(ov_ctx* c, EigSet& E);
+// tensor-core projection (proj_tc.cu): c[i][r] = eta_i^dag psi_r, device double2 [nev][R]
+int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st);
+int proj_tc_status(ov_ctx* c, cudaStream_t st);
 
 }  // namespace ov

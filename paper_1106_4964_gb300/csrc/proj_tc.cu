@@ -1,0 +1,382 @@
+// Low-mode projection c = eta^dag psi (Eqs. 6-7, 9) on the 5th-generation
+// tensor cores: the one dense contraction on the path.
+//
+// As a real GEMM: A = the eigenvectors, one row per eigenvector, each row the
+// 24V reals of the field in the internal FP32 order (re, im interleaved),
+// stored as bf16; B = two real columns per right-hand side, b1 = psi (re, im)
+// and b2 = (im, -re), so that sum_k A_ik b1_k = Re(eta_i^dag psi) and
+// sum_k A_ik b2_k = Im(eta_i^dag psi).  D[128 x N] = A[128 x K] B[K x N] is
+// split over K across the CTAs: each CTA streams its K range through a
+// 4-stage ring of shared-memory tiles filled by TMA (128B swizzle, K-major),
+// one thread issues tcgen05.mma (kind::f16, bf16 in, FP32 accumulate in
+// TMEM), the accumulator is read back with tcgen05.ld and written as FP32
+// partial sums, and a second kernel adds the partials in a fixed order in
+// FP64.  Rows beyond the number of eigenvectors and columns beyond 2R are
+// zero-filled by the TMA bounds.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel records an
+// error code, stops issuing work, waits (bounded) for its own copies and
+// MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "ctx.h"
+
+namespace ov {
+
+namespace {
+
+constexpr int TC_M = 128;         // rows of the MMA tile (eigenvectors per launch)
+constexpr int TC_BK = 64;         // K elements per stage (128 bytes of bf16: one swizzle atom row)
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 128;
+constexpr long long TC_SPIN = 1ll << 22;  // bounded wait (iterations of try_wait, ~seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+{
+    for (long long i = 0; i < TC_SPIN; ++i)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(const void* p)
+{
+    const uint64_t addr = smem_u32(p);
+    return ((addr >> 4) & 0x3FFFull)     // start address
+           | (1ull << 16)                // leading byte offset (unused for swizzled K-major)
+           | ((1024ull >> 4) << 32)      // stride byte offset: 8 rows x 128 bytes
+           | (1ull << 46)                // descriptor version
+           | (2ull << 61);               // 128-byte swizzle
+}
+
+// instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major, M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4)                     // D: f32
+           | (1u << 7)                   // A: bf16
+           | (1u << 10)                  // B: bf16
+           | ((uint32_t)(N >> 3) << 17)  // N / 8
+           | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// partials[blockIdx.x][row][col] (FP32), row < 128, col < npad; K range split evenly over the grid
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    proj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ktiles,
+                   int npad, int tmem_cols, float* __restrict__ partials, int* err)
+{
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    // 1024-byte aligned stage buffers (swizzle atoms)
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    const int a_bytes = TC_M * TC_BK * 2;
+    const int b_bytes = npad * TC_BK * 2;
+    const int stage_bytes = a_bytes + b_bytes;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = (ktiles + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * per;
+    const int nt = max(0, min(ktiles, t0 + per) - t0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    int issued = 0;  // tiles whose MMAs were issued (MMA thread)
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads into the stage ring
+        for (int t = 0; t < nt; ++t) {
+            const int s = t % TC_STAGES;
+            const uint32_t ph = (t / TC_STAGES) & 1;
+            if (t >= TC_STAGES && !mbar_wait(&empty_bar[s], ph ^ 1)) {
+                atomicExch(err, 1);
+                abort_flag = 1;
+                break;
+            }
+            if (*(volatile int*)&abort_flag) break;
+            uint8_t* sa = base + s * stage_bytes;
+            mbar_expect_tx(&full_bar[s], stage_bytes);
+            const int k = (t0 + t) * TC_BK;
+            tma_load_2d(sa, &tmA, k, 0, &full_bar[s]);
+            tma_load_2d(sa + a_bytes, &tmB, k, 0, &full_bar[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(TC_M, npad);
+        for (int t = 0; t < nt; ++t) {
+            const int s = t % TC_STAGES;
+            const uint32_t ph = (t / TC_STAGES) & 1;
+            if (!mbar_wait(&full_bar[s], ph)) {
+                atomicExch(err, 2);
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t* sa = base + s * stage_bytes;
+            uint8_t* sb = sa + a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                mma_bf16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (t > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty_bar[s]);  // frees the stage when these MMAs have read it
+            ++issued;
+        }
+        mma_commit(&done_bar);  // arrives when every issued MMA has completed
+    }
+    __syncthreads();
+    // wait for the accumulator (bounded); with no tile the done barrier still completes (empty commit)
+    bool ok = mbar_wait(&done_bar, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* out = partials + (size_t)blockIdx.x * TC_M * npad;
+    const int row = warp * 32 + lane;
+    for (int c0 = 0; c0 < npad; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[(size_t)row * npad + c0 + j] = (ok && issued >= 0 && nt > 0) ? v[j] : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// c[i][r] = (sum_g P[g][i][2r], sum_g P[g][i][2r+1]) in FP64, fixed order
+__global__ void proj_tc_reduce(const float* partials, int ngrid, int npad, int nev, int nrhs, double2* c)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nev * nrhs) return;
+    const int i = k / nrhs, r = k % nrhs;
+    double re = 0, im = 0;
+    for (int g = 0; g < ngrid; ++g) {
+        const float* p = partials + ((size_t)g * TC_M + i) * npad;
+        re += p[2 * r];
+        im += p[2 * r + 1];
+    }
+    c[k] = make_double2(re, im);
+}
+
+// B operand: rows 2r = psi_r, 2r+1 = (im, -re) pairs, bf16, from an FP32 field
+__global__ void build_b_kernel(const float4* __restrict__ x, int n4, int nrhs, __nv_bfloat16* B, long long K)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (q >= n4 || r >= nrhs) return;
+    const float4 v = x[(size_t)r * n4 + q];
+    __nv_bfloat162* b1 = reinterpret_cast<__nv_bfloat162*>(B + (size_t)(2 * r) * K + 4 * q);
+    __nv_bfloat162* b2 = reinterpret_cast<__nv_bfloat162*>(B + (size_t)(2 * r + 1) * K + 4 * q);
+    b1[0] = __floats2bfloat162_rn(v.x, v.y);
+    b1[1] = __floats2bfloat162_rn(v.z, v.w);
+    b2[0] = __floats2bfloat162_rn(v.y, -v.x);
+    b2[1] = __floats2bfloat162_rn(v.w, -v.z);
+}
+
+__global__ void to_bf16_kernel(const float4* __restrict__ x, long long n4, __nv_bfloat16* y)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n4) return;
+    const float4 v = x[q];
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(y + 4 * q);
+    o[0] = __floats2bfloat162_rn(v.x, v.y);
+    o[1] = __floats2bfloat162_rn(v.z, v.w);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D bf16 map: rows x K (K contiguous), box 64 x box_rows, 128B swizzle, zero fill outside
+bool make_map(CUtensorMap* m, const void* ptr, long long K, int rows, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// bf16 copy of the eigenvectors (rows of A), built once from the FP32 copy
+int eig_bf16_rows(ov_ctx* c, int which, cudaStream_t st, const void** out)
+{
+    EigSet& E = c->eig[which];
+    if (!E.nev) return set_err(c, OV_ESTATE, "no eigenpairs stored (which=%d)", which);
+    if (!E.tc_rows) {
+        FieldDesc f32;
+        OV_TRY(eig_vectors(c, which, P_F32, st, &f32));
+        const long long K = 48LL * c->g.Vh;
+        OV_TRY(dev_alloc(c, &E.tc_rows, (size_t)E.nev * K * 2));
+        E.tc_bytes = (size_t)E.nev * K * 2;
+        const long long n4 = (long long)E.nev * K / 4;
+        to_bf16_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>((const float4*)f32.data, n4,
+                                                                     (__nv_bfloat16*)E.tc_rows);
+        OV_CUDA(c, cudaGetLastError());
+    }
+    *out = E.tc_rows;
+    return OV_OK;
+}
+
+// c[i][r] = eta_i^dag psi_r (double2 [nev][R] device) on the tensor cores; psi any precision
+int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st)
+{
+    EigSet& E = c->eig[which];
+    const int nev = E.nev, R = psi.nrhs;
+    if (nev < 1 || nev > TC_M) return set_err(c, OV_EINVAL, "tensor-core projection: nev = %d outside 1..128", nev);
+    const int npad = ((2 * R + 15) / 16) * 16;
+    if (npad > 256) return set_err(c, OV_EINVAL, "tensor-core projection: too many right-hand sides");
+    const long long K = 48LL * c->g.Vh;
+    if (K % TC_BK) return set_err(c, OV_EINVAL, "tensor-core projection: 24V must be a multiple of 64");
+    const void* A = nullptr;
+    OV_TRY(eig_bf16_rows(c, which, st, &A));
+    // psi as FP32 (internal order), then the bf16 B rows
+    FieldDesc p32 = psi;
+    if (psi.prec != P_F32) {
+        OV_TRY(ws_field(c, WS_AUX0, P_F32, R, &p32));
+        OV_TRY(convert(c, psi, p32, st));
+    }
+    const size_t bbytes = (size_t)2 * R * K * 2;
+    if (c->tc_b_bytes < bbytes) {
+        if (c->tc_b) {
+            cudaDeviceSynchronize();
+            dev_free(c, c->tc_b, c->tc_b_bytes);
+        }
+        c->tc_b = nullptr;
+        c->tc_b_bytes = 0;
+        graphs_clear(c);
+        OV_TRY(dev_alloc(c, &c->tc_b, bbytes));
+        c->tc_b_bytes = bbytes;
+    }
+    const long long n4 = K / 4;
+    build_b_kernel<<<dim3((unsigned)((n4 + 255) / 256), R), 256, 0, st>>>((const float4*)p32.data, (int)n4, R,
+                                                                           (__nv_bfloat16*)c->tc_b, K);
+    OV_CUDA(c, cudaGetLastError());
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, K, nev, TC_M) || !make_map(&mb, c->tc_b, K, 2 * R, npad))
+        return set_err(c, OV_ECUDA, "cuTensorMapEncodeTiled failed");
+    const int ktiles = (int)(K / TC_BK);
+    const int grid = std::min(ktiles, 2 * 152);
+    const size_t smem = (size_t)TC_STAGES * (TC_M + npad) * TC_BK * 2 + 1024;
+    OV_TRY(ensure_partials(c, (size_t)grid * TC_M * npad * sizeof(float)));
+    if (!c->tc_err) {
+        void* p = nullptr;
+        OV_TRY(dev_alloc(c, &p, sizeof(int)));
+        c->tc_err = (int*)p;
+        OV_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), st));
+    }
+    OV_CUDA(c, cudaFuncSetAttribute(proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : (npad <= 128 ? 128 : 256));
+    proj_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ktiles, npad, tmem_cols, (float*)c->partials, c->tc_err);
+    OV_CUDA(c, cudaGetLastError());
+    proj_tc_reduce<<<(nev * R + 127) / 128, 128, 0, st>>>((const float*)c->partials, grid, npad, nev, R, cout);
+    OV_CUDA(c, cudaGetLastError());
+    return OV_OK;
+}
+
+int proj_tc_status(ov_ctx* c, cudaStream_t st)
+{
+    if (!c->tc_err) return OV_OK;
+    int h = 0;
+    OV_CUDA(c, cudaMemcpyAsync(&h, c->tc_err, sizeof h, cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    if (h) {
+        cudaMemsetAsync(c->tc_err, 0, sizeof(int), st);
+        return set_err(c, OV_ETIMEOUT, "tensor-core projection: bounded wait gave up (stage %d)", h);
+    }
+    return OV_OK;
+}
+
+}  // namespace ov

@@ -485,11 +485,7 @@ int store_eigs(ov_ctx* c, int which, const FieldDesc& vecs, const std::vector<in
 {
     EigSet& E = c->eig[which];
     graphs_clear(c);
-    for (auto& f : E.vec) field_free(c, &f);
-    if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
-    E.d_sign = nullptr;
-    E.nev = 0;
-    E.vals.clear();
+    eig_clear(c, E);
     const int nev = (int)pick.size();
     OV_TRY(field_alloc(c, P_F64, nev, &E.vec[P_F64]));
     std::vector<double> sg(nev);
