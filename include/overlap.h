@@ -220,7 +220,9 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *                    tol < 1e-7 and FP32 otherwise (Gram-Schmidt and
  *                    Rayleigh-Ritz stay FP64), or an ov_prec value;
  *   "proj_tc" (1):    16-bit overlap: compute eta^dag psi on the tensor cores
- *                    (0: on the CUDA cores). */
+ *                    (0: on the CUDA cores);
+ *   "net_sym" (1):    flexible CG applies the learned preconditioner as
+ *                    (M + M^dag) / 2 (Hermitian) instead of M. */
 int ov_set_option(ov_ctx* ctx, const char* name, double value);
 /* Launch configuration of the dslash for (prec, nrhs): block = bx sites x by
  * right-hand sides, and a register-budget variant (0: unbounded; 1, 2:

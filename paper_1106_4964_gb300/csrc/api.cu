@@ -887,6 +887,8 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
     } else if (n == "proj_tc") {
         graphs_clear(c);
         c->proj_tc = value != 0;
+    } else if (n == "net_sym") {
+        c->net_sym = value != 0;
     } else {
         return set_err(c, OV_EINVAL, "unknown option '%s'", name);
     }
@@ -905,8 +907,9 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
-    if (variant < 0 || variant >= DSLASH_VARIANTS) return set_err(c, OV_EINVAL, "bad variant %d", variant);
-    const int maxt = variant == 0 ? (prec == P_F64 ? 256 : 512) : 256;
+    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant == 3 && (prec == P_F64 || by != 1)))
+        return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
+    const int maxt = variant == 0 ? (prec == P_F64 ? 256 : 512) : (variant == 3 ? 128 : 256);
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
     c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
@@ -927,11 +930,13 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
     // candidates: block = x sites by y right-hand sides, times the register-budget variants
     std::vector<std::tuple<int, int, int>> cand;
     for (int v = 0; v < DSLASH_VARIANTS; ++v) {
-        const int maxt = v == 0 ? (prec == P_F64 ? 256 : 512) : 256;
+        if (v == 3 && prec == P_F64) continue;  // staged variant: FP32 arithmetic only
+        const int maxt = v == 0 ? (prec == P_F64 ? 256 : 512) : (v == 3 ? 128 : 256);
         for (int x : {32, 64, 128, 256})
             for (int y = 1; y <= nrhs && y <= 16; ++y) {
+                if (v == 3 && y != 1) continue;
                 if (nrhs % y && y != nrhs) continue;
-                if (x * y > maxt || x * y < 64) continue;
+                if (x * y > maxt || x * y < (v == 3 ? 32 : 64)) continue;
                 cand.push_back(std::make_tuple(x, y, v));
             }
     }

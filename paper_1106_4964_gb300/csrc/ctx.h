@@ -33,7 +33,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
-    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
+    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
 
@@ -94,6 +94,7 @@ struct ov_ctx {
     int filter_dd = 8;            // Chebyshev filter degree on D^dag D (deflate which = 1)
     int eig_prec = -1;            // operator precision inside deflate: -1 automatic, else ov_prec
     int proj_tc = 1;              // 16-bit overlap: low-mode projection on the tensor cores
+    int net_sym = 1;              // learned preconditioner applied as (M + M^dag) / 2
 
     // tensor-core projection buffers (proj_tc.cu)
     void* tc_b = nullptr;

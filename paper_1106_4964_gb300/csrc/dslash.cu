@@ -149,6 +149,9 @@ __device__ __forceinline__ void hop(const DslashArgs& A, const char* in_q, const
     accumulate<MU, S, Real>(acc, chi);
 }
 
+template <int SP, int NY>
+__device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int s, const real_t<SP> acc[24]);
+
 // Register-budget variants chosen by the autotuner: VAR 0 lets the compiler
 // use what it wants (low occupancy, long latency chains), VAR 1 and 2 cap
 // the registers so that more warps are resident to hide load latency.
@@ -195,7 +198,17 @@ __global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) 
     hop<SP, GP, 3, +1>(A, in_q, inn_q, p, s, cb_index(g, x, y, z, tp), tp == 0, acc);
     hop<SP, GP, 3, -1>(A, in_q, inn_q, p, s, cb_index(g, x, y, z, tm), t == 0, acc);
 
-    // epilogue
+    epilogue<SP, NY>(A, r, p, s, acc);
+}
+
+// out(n) = g5_out[ g5_core(a psi(n) + b acc) + sum_j sy_j y_j(n) ], stored in the field format
+template <int SP, int NY>
+__device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int s, const real_t<SP> acc[24])
+{
+    using Real = real_t<SP>;
+    const Geom& g = A.g;
+    constexpr size_t CH = (SP == P_F64 ? 12 : (SP == P_F32 ? 6 : 3)) * 16;
+    const size_t par_bytes = CH * g.Vh;
     const size_t off = ((size_t)r * 2 + p) * par_bytes;
     const size_t noff = ((size_t)r * 2 + p) * g.Vh;
     Real o[24];
@@ -225,6 +238,222 @@ __global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) 
     store_spinor<SP, Real>(A.out + off, A.out_n ? A.out_n + noff : nullptr, g.Vh, s, o);
 }
 
+// ---------------------------------------------------------------------------
+// Variant 3 (FP32 arithmetic only): every thread stages the 8 neighbour
+// spinors and links of its site into its own shared-memory slots with
+// cp.async, one commit group per hop, so all of a site's loads are in flight
+// at once without occupying registers; hop h then waits only for group h.
+// Slots are chunk-major ([hop][chunk][thread]) so a warp's accesses hit
+// consecutive 16-byte words.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int SP, int GP>
+struct AsyncLayout {
+    static constexpr int SCH = nchunk_dev<SP>();                  // 16-byte spinor chunks
+    static constexpr int LCB = GP == P_F32 ? 16 : 8;              // bytes of each of the 3 link chunks
+    static constexpr int NRM = (SP == P_F16 || SP == P_BF16) ? 4 : 0;
+    static constexpr int PER_THREAD = 8 * (SCH * 16 + 3 * LCB + NRM);
+    __device__ static uint8_t* spin(uint8_t* sm, int BX, int h, int k, int t) { return sm + ((h * SCH + k) * BX + t) * 16; }
+    __device__ static uint8_t* link(uint8_t* sm, int BX, int h, int k, int t)
+    {
+        return sm + 8 * SCH * 16 * BX + ((h * 3 + k) * BX + t) * LCB;
+    }
+    __device__ static uint8_t* norm(uint8_t* sm, int BX, int h, int t)
+    {
+        return sm + 8 * (SCH * 16 + 3 * LCB) * BX + (h * BX + t) * 4;
+    }
+};
+
+template <int SP, int GP>
+__device__ __forceinline__ void stage_hop(uint8_t* sm, int BX, int t, int h, const char* in_q, const float* inn_q,
+                                          int Vh, int sn, const char* lbase, int ls)
+{
+    using L = AsyncLayout<SP, GP>;
+#pragma unroll
+    for (int k = 0; k < L::SCH; ++k) cp_async16(L::spin(sm, BX, h, k, t), in_q + ((size_t)k * Vh + sn) * 16);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if constexpr (L::LCB == 16)
+            cp_async16(L::link(sm, BX, h, k, t), lbase + ((size_t)k * Vh + ls) * 16);
+        else
+            cp_async8(L::link(sm, BX, h, k, t), lbase + ((size_t)k * Vh + ls) * 8);
+    }
+    if constexpr (L::NRM) cp_async4(L::norm(sm, BX, h, t), inn_q + sn);
+    cp_async_commit();
+}
+
+template <int SP, int GP, int MU, int S, int H>
+__device__ __forceinline__ void hop_staged(uint8_t* sm, int BX, int t, bool cross, float phase, float acc[24])
+{
+    using L = AsyncLayout<SP, GP>;
+    cp_async_wait<7 - H>();
+    float v[24];
+    if constexpr (SP == P_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(L::spin(sm, BX, H, k, t));
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = a.z;
+            v[4 * k + 3] = a.w;
+        }
+    } else {
+        const float n = *reinterpret_cast<const float*>(L::norm(sm, BX, H, t));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 a = *reinterpret_cast<const uint4*>(L::spin(sm, BX, H, k, t));
+            const float2 a0 = Half<SP>::to2(a.x), a1 = Half<SP>::to2(a.y), a2 = Half<SP>::to2(a.z),
+                         a3 = Half<SP>::to2(a.w);
+            v[8 * k + 0] = a0.x * n;
+            v[8 * k + 1] = a0.y * n;
+            v[8 * k + 2] = a1.x * n;
+            v[8 * k + 3] = a1.y * n;
+            v[8 * k + 4] = a2.x * n;
+            v[8 * k + 5] = a2.y * n;
+            v[8 * k + 6] = a3.x * n;
+            v[8 * k + 7] = a3.y * n;
+        }
+    }
+    float h[12];
+    project<MU, S, float>(v, h);
+    if (cross) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) h[i] *= phase;
+    }
+    float u[18];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if constexpr (GP == P_F32) {
+            const float4 a = *reinterpret_cast<const float4*>(L::link(sm, BX, H, k, t));
+            u[4 * k] = a.x;
+            u[4 * k + 1] = a.y;
+            u[4 * k + 2] = a.z;
+            u[4 * k + 3] = a.w;
+        } else {
+            const uint2 a = *reinterpret_cast<const uint2*>(L::link(sm, BX, H, k, t));
+            const float2 a0 = Half<GP>::to2(a.x), a1 = Half<GP>::to2(a.y);
+            u[4 * k] = a0.x;
+            u[4 * k + 1] = a0.y;
+            u[4 * k + 2] = a1.x;
+            u[4 * k + 3] = a1.y;
+        }
+    }
+    // row 2 = conj(row0 x row1)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int a = (j + 1) % 3, b = (j + 2) % 3;
+        const float re = u[2 * a] * u[2 * (3 + b)] - u[2 * a + 1] * u[2 * (3 + b) + 1] -
+                         (u[2 * b] * u[2 * (3 + a)] - u[2 * b + 1] * u[2 * (3 + a) + 1]);
+        const float im = u[2 * a] * u[2 * (3 + b) + 1] + u[2 * a + 1] * u[2 * (3 + b)] -
+                         (u[2 * b] * u[2 * (3 + a) + 1] + u[2 * b + 1] * u[2 * (3 + a)]);
+        u[12 + 2 * j] = re;
+        u[12 + 2 * j + 1] = -im;
+    }
+    float chi[12];
+    link_mul<S, float>(u, h, chi);
+    accumulate<MU, S, float>(acc, chi);
+}
+
+template <int SP, int GP, int NY>
+__global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int BX = blockDim.x, tx = threadIdx.x;
+    const int p = blockIdx.x & 1;
+    const int s = (blockIdx.x >> 1) * BX + tx;
+    const int r = blockIdx.y;
+    const Geom& g = A.g;
+    if (s >= g.Vh || r >= A.nrhs) return;
+    constexpr size_t CH = nchunk_dev<SP>() * 16;
+    const size_t par_bytes = CH * g.Vh;
+    const int q = 1 - p;
+    const char* in_q = A.in + ((size_t)r * 2 + q) * par_bytes;
+    const float* inn_q = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
+    int c[4];
+    cb_coords(g, s, p, c);
+    const int x = c[0], y = c[1], z = c[2], t = c[3];
+    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
+    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
+    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
+    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
+    const int sn[8] = {cb_index(g, xp, y, z, t), cb_index(g, xm, y, z, t), cb_index(g, x, yp, z, t),
+                       cb_index(g, x, ym, z, t), cb_index(g, x, y, zp, t), cb_index(g, x, y, zm, t),
+                       cb_index(g, x, y, z, tp), cb_index(g, x, y, z, tm)};
+    constexpr size_t LB = gauge_link_bytes_dev<GP>();
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int mu = h >> 1;
+        const bool fwd = (h & 1) == 0;
+        const int lpar = fwd ? p : q, ls = fwd ? s : sn[h];
+        stage_hop<SP, GP>(sm, BX, tx, h, in_q, inn_q, g.Vh, sn[h], A.gauge + ((size_t)(lpar * 4 + mu) * g.Vh) * LB, ls);
+    }
+    float acc[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp == 0, (float)g.bc[0], acc);
+    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, x == 0, (float)g.bc[0], acc);
+    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp == 0, (float)g.bc[1], acc);
+    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, y == 0, (float)g.bc[1], acc);
+    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp == 0, (float)g.bc[2], acc);
+    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, z == 0, (float)g.bc[2], acc);
+    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp == 0, (float)g.bc[3], acc);
+    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, t == 0, (float)g.bc[3], acc);
+    epilogue<SP, NY>(A, r, p, s, acc);
+}
+
+template <int SP, int GP>
+cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
+{
+    if constexpr (SP == P_F64) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (block.y != 1 || block.x > 128) return cudaErrorInvalidValue;
+        const size_t shm = (size_t)block.x * AsyncLayout<SP, GP>::PER_THREAD;
+        static bool attr_set[4] = {false, false, false, false};
+        if (!attr_set[ny]) {
+            cudaError_t e = cudaSuccess;
+            switch (ny) {
+            case 0: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
+            case 1: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
+            case 2: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
+            case 3: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
+            default: return cudaErrorInvalidValue;
+            }
+            if (e != cudaSuccess) return e;
+            attr_set[ny] = true;
+        }
+        dim3 g2(grid.x, A.nrhs);
+        switch (ny) {
+        case 0: dslash_staged_kernel<SP, GP, 0><<<g2, block, shm, st>>>(A); break;
+        case 1: dslash_staged_kernel<SP, GP, 1><<<g2, block, shm, st>>>(A); break;
+        case 2: dslash_staged_kernel<SP, GP, 2><<<g2, block, shm, st>>>(A); break;
+        case 3: dslash_staged_kernel<SP, GP, 3><<<g2, block, shm, st>>>(A); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+}
+
 template <int SP, int GP, int VAR>
 cudaError_t launch_var(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
 {
@@ -246,6 +475,7 @@ cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 bloc
     case 0: return launch_var<SP, GP, 0>(A, ny, grid, block, st);
     case 1: return launch_var<SP, GP, 1>(A, ny, grid, block, st);
     case 2: return launch_var<SP, GP, 2>(A, ny, grid, block, st);
+    case 3: return launch_staged<SP, GP>(A, ny, grid, block, st);
     }
     return cudaErrorInvalidValue;
 }

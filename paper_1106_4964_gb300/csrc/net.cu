@@ -38,6 +38,7 @@ struct NetState {
     float2* partials = nullptr;
     size_t partials_n = 0;
     int adam_t = 0;
+    int adj_valid = 0;  // Wadj matches W
     // recorded training pairs: residuals and iterates (then errors), f32 single-rhs fields
     int recording = 0;
     FieldDesc pr{}, px{};
@@ -410,16 +411,32 @@ void net_free(ov_ctx* c)
 int net_apply_precond(ov_ctx* c, const FieldDesc& r, const FieldDesc& z, cudaStream_t st)
 {
     if (!c->net) return set_err(c, OV_ESTATE, "learned preconditioner has no weights");
-    FieldDesc h, a, b;
+    NetState* n = c->net;
+    const bool sym = c->net_sym != 0;
+    if (sym && !n->adj_valid) {
+        OV_TRY(refresh_adjoint(c, st));
+        n->adj_valid = 1;
+    }
+    FieldDesc h, a, b, d;
     OV_TRY(ws_field(c, WS_NET_H, P_F32, NET_C, &h));
     OV_TRY(ws_field(c, WS_NET_G, P_F32, 1, &a));
     OV_TRY(ws_field(c, WS_NET_GH, P_F32, 1, &b));
+    if (sym) OV_TRY(ws_field(c, WS_NET_S, P_F32, 1, &d));
     for (int q = 0; q < r.nrhs; ++q) {
         FieldDesc rq = one(r, q), zq = one(z, q);
         const bool f32in = r.prec == P_F32, f32out = z.prec == P_F32;
         if (!f32in) OV_TRY(convert(c, rq, a, st));
-        OV_TRY(layer_fwd(c, 0, false, f32in ? rq : a, h, st));
-        OV_TRY(layer_fwd(c, 1, false, h, f32out ? zq : b, st));
+        const FieldDesc& x = f32in ? rq : a;
+        OV_TRY(layer_fwd(c, 0, false, x, h, st));
+        OV_TRY(layer_fwd(c, 1, false, h, (f32out && !sym) ? zq : b, st));
+        if (sym) {
+            // z = (M + M^dag) r / 2, M^dag = L1^dag L2^dag: Hermitian, as CG expects of a preconditioner
+            OV_TRY(layer_fwd(c, 1, true, x, h, st));
+            OV_TRY(layer_fwd(c, 0, true, h, d, st));
+            FieldDesc v[2] = {b, d};
+            double2 hc[2] = {make_double2(0.5, 0), make_double2(0.5, 0)};
+            OV_TRY(lincomb(c, f32out ? zq : b, 2, v, hc, nullptr, 0, nullptr, st));
+        }
         if (!f32out) OV_TRY(convert(c, b, zq, st));
     }
     return OV_OK;
@@ -452,6 +469,7 @@ int ov_net_set_weights(ov_ctx* c, const double* w, int n)
     for (int i = 0; i < NET_PARAMS; ++i) h[i] = make_float2((float)w[2 * i], (float)w[2 * i + 1]);
     OV_CUDA(c, cudaMemcpy(c->net->W, h.data(), sizeof(float2) * NET_PARAMS, cudaMemcpyHostToDevice));
     c->net->trained = 1;
+    c->net->adj_valid = 0;
     return OV_OK;
 }
 
@@ -612,9 +630,10 @@ int ov_net_train(ov_ctx* c, int nsolves, int steps, double lr, double mass, doub
                                                                    1.0f / (float)n->npairs);
         OV_CUDA(c, cudaGetLastError());
     }
-    OV_TRY(loss_grad(c, n->pr, n->px, 0, n->npairs, &loss, st));
+    OV_TRY(loss_grad(c, n->pr, n->px, 0, n->npairs, &loss, st));  // also refreshes the adjoint weights
     if (final_loss) *final_loss = loss / n->npairs;
     n->trained = 1;
+    n->adj_valid = 1;
     return OV_OK;
 }
 

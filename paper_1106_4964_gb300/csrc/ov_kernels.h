@@ -23,9 +23,9 @@ struct DslashArgs {
     int nrhs;
     int g5_core, g5_out;
 };
-// var: register-budget variant (0 unbounded, 1 and 2 capped for occupancy)
+// var: 0 unbounded registers, 1 and 2 capped for occupancy, 3 shared-memory staging (FP32 math, by = 1)
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st);
-constexpr int DSLASH_VARIANTS = 3;
+constexpr int DSLASH_VARIANTS = 4;
 
 // ---------------------------------------------------------------- layout conversion
 // canonical complex128 [nrhs][V][12] (device) <-> internal field
