@@ -156,7 +156,11 @@ def run_gpu(args):
     prec = "f32"
     fi, fo = ctx.field(1, prec), ctx.field(1, prec)
     fi.load(psi_dev)
-    bx, by, var = ctx.tune_dslash(prec, 1)
+    if args.shape:
+        bx, by, var = args.shape
+        ctx.set_dslash_shape(prec, 1, bx, by, var)
+    else:
+        bx, by, var = ctx.tune_dslash(prec, 1)
     st = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.dslash_field(fi, fo, -RHO)
@@ -576,6 +580,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("BX", "BY", "VARIANT"),
+                    help="fixed dslash launch configuration instead of the autotuner (profiling)")
     ap.add_argument("--workload", default="dslash", choices=["dslash", "overlap", "propagator", "learned", "project"])
     ap.add_argument("--dims", type=int, nargs=4, default=None)
     ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 32])

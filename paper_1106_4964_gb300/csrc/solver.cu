@@ -367,8 +367,18 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
     const int jcut = std::min((int)ritz0.size() - 1, nev + std::max(4, nev / 2));
     double acut = ritz0[jcut];
     if (!(acut < bmax)) acut = 0.5 * bmax;
+    // Cap the degree so that the filter's dynamic range, bounded by T_K at x = 0, stays within what
+    // the work precision resolves: otherwise rounding relative to the largest filtered eigenvalue
+    // swamps the smaller wanted ones (1e12 for FP64 work fields, 1e4 for FP32).
+    int Keff = K;
+    if (K > 0) {
+        const double y0 = (bmax + acut) / (bmax - acut);
+        const double limit = W.tmp[0].prec == P_F64 ? 1e12 : 1e4;
+        const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
+        Keff = std::max(2, std::min(K, kmax));
+    }
     OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
-        OV_TRY(cheb_filter(c, AcW, K, acut, bmax, in, o, W.tmp, st));
+        OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, in, o, W.tmp, st));
         return project_chiral(c, o, chi, st);
     };
 
@@ -410,7 +420,9 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             const double r = beta * std::abs(Y[(size_t)(m - 1) * m + order[i]]);
             if (r <= tolF * std::fabs(theta[order[i]])) ++nconv;
         }
-        if (nconv == nev) {
+        // Rayleigh-Ritz when the filter's Ritz pairs look converged, and every 4th restart anyway
+        // (the filter residuals are pessimistic for the smaller wanted filter values)
+        if (nconv == nev || restart % 4 == 3) {
             // Rayleigh-Ritz with R in the span of the nev leading Ritz vectors (basis untouched)
             std::vector<cd> Yk((size_t)m * nev);
             for (int i = 0; i < m; ++i)
@@ -461,8 +473,7 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            tolF *= 1e-2;
-            if (tolF < 1e-16) break;
+            if (nconv == nev) tolF = std::max(tolF * 1e-2, 1e-15);  // Ritz pairs of F need more accuracy
         }
         // thick restart with the kkeep leading Ritz vectors
         std::vector<cd> Yk((size_t)m * kkeep);
@@ -523,7 +534,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const int kkeep = std::min(m - 1, ns + (m - ns) / 3);
     // operator precision: FP64 when the eigen-residual target needs it; an FP32 filter (FP64
     // Gram-Schmidt and Rayleigh-Ritz) when tol >= 1e-7, or as set by ov_set_option("eig_prec")
-    const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-7 ? P_F32 : P_F64);
+    const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : P_F64);
 
     LanczosWork W{};
     FieldDesc outv{}, tsa{}, tsb{}, ta{};
