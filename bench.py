@@ -35,7 +35,7 @@ DIMS = (24, 24, 24, 64)
 BC = (1.0, 1.0, 1.0, -1.0)
 RHO = 1.5
 METRIC = "dslash GB/s & GFLOP/s (% HBM roofline); overlap propagator solves/s at res 1e-10"
-REAL_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+REAL_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "df64": 8}
 FLOP_SITE = 1320
 
 
@@ -197,14 +197,14 @@ def run_gpu(args):
     # ---- variants (same workload, other precisions and 12 rhs)
     variants = {}
     if not args.quick:
-        for p in ("f64", "f16", "bf16"):
+        for p in ("f64", "df64", "f16", "bf16"):
             t = time_dslash(ctx, U_dev, psi_dev, p, 1, min(2000, max(5, args.steps)), args.warmup, torch)
             b = V * site_bytes(p, 1)
             variants[f"{p}_r1"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
                                    "GFLOPps": round(FLOP_SITE * V / t / 1e6, 1),
                                    "frac_hbm": round(b / t / 1e6 / hbm, 3)}
         psi12 = torch.from_numpy(make_inputs_rhs(12)).cuda()
-        for p in ("f32", "f16", "f64"):
+        for p in ("f32", "f16", "f64", "df64"):
             t = time_dslash(ctx, U_dev, psi12, p, 12, min(300, max(3, args.steps // 2)), args.warmup, torch)
             b = V * 12 * site_bytes(p, 12)
             variants[f"{p}_r12"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
@@ -364,7 +364,7 @@ def run_overlap(args):
     psi12 = torch.from_numpy(synth.gaussian_spinor(dims, seed=3, nrhs=12)).cuda()
     ref = None
     res = {}
-    for prec in ("f64", "f32", "f16", "bf16"):
+    for prec in ("f64", "df64", "f32", "f16", "bf16"):
         for nrhs, src in ((1, psi), (12, psi12)):
             if nrhs == 12 and prec == "f64" and not args.f64_r12:
                 continue
@@ -474,6 +474,7 @@ def run_propagator(args):
     ctx = ov.Context(dims, BC)
     ctx.set_gauge(torch.from_numpy(U).cuda())
     ctx.set_option("reliable_delta", args.delta)
+    ctx.set_option("hi_prec", ov.PREC[args.hi_prec])
     setup = {}
     t0 = time.perf_counter()
     ctx.set_sign_poly(RHO, 0.05, args.degree, 0.0)
@@ -487,13 +488,14 @@ def run_propagator(args):
         vals, _ = ctx.get_eigenpairs(0)
         eps = (0.99 * np.abs(vals).max() / lmax) ** 2
     ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+    ctx.set_option("chiral", int(args.chiral))
     if args.nev_cg > 0:
         ctx.set_option("filter_dd", args.filter_dd)
         t0 = time.perf_counter()
         ctx.deflate(1, args.nev_cg, args.eig_tol)
         setup["deflate_dd"] = time.perf_counter() - t0
     b = torch.from_numpy(synth.point_sources(dims)).cuda()
-    for p in ("f32", "f16", "f64"):
+    for p in ("f32", "f16", args.hi_prec):
         ctx.tune_dslash(p, 12)
     out = {}
     for inner in args.cg_inner.split(","):
@@ -507,11 +509,13 @@ def run_propagator(args):
     print(json.dumps({
         "metric": "overlap propagator solves/s at res 1e-10", "value": best["solves_per_s"], "unit": "solves/s",
         "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(1e3 * best["seconds"], 1),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed f32/f16 + f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"mixed {args.cg_inner.replace(',', '/')} + {args.hi_prec}",
         "data": "synthetic",
         "config": {"workload": f"12 point sources, {dims[0]}^3x{dims[3]}, rho 1.5, mass {args.mass}, "
                                f"{args.nev} H_w modes + {args.nev_cg} D^dag D modes, degree {args.degree}",
-                   "lattice": list(dims), "eps": eps, "lambda_max": lmax},
+                   "lattice": list(dims), "eps": eps, "lambda_max": lmax, "hi_prec": args.hi_prec,
+                   "chiral": bool(args.chiral)},
         "propagators_per_s": round(best["solves_per_s"] / 12, 5),
         "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out}))
 
@@ -593,6 +597,10 @@ def main():
     ap.add_argument("--mass", type=float, default=0.0)
     ap.add_argument("--delta", type=float, default=0.1)
     ap.add_argument("--cg-inner", default="f32", help="inner precisions of the propagator CG, comma separated")
+    ap.add_argument("--chiral", type=int, default=0, choices=[0, 1],
+                    help="propagator CG and D^dag D deflation on chiral sectors (one sign per application)")
+    ap.add_argument("--hi-prec", default="f64", choices=["f64", "df64"],
+                    help="accurate arithmetic of the propagator CG (true residuals): FP64 or double-float")
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64-r12", action="store_true")

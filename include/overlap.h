@@ -35,8 +35,10 @@
  *    output is guaranteed and ov_last_error() describes the failure.
  *  - Precision (ov_prec): OV_F64 stores and computes in FP64; OV_F32 in FP32;
  *    OV_F16S / OV_BF16S store spinors and links in 16 bits (spinors with one
- *    FP32 scale per site) and compute in FP32.  Dot products and norms always
- *    accumulate in FP64.
+ *    FP32 scale per site) and compute in FP32; OV_DF64 stores every real as an
+ *    unevaluated sum of two FP32 numbers (8 bytes, about 48 significand bits)
+ *    and computes with error-free FP32 transformations, an FP64-class result
+ *    on the FP32 pipes.  Dot products and norms always accumulate in FP64.
  */
 #ifndef OVERLAP_GB300_H
 #define OVERLAP_GB300_H
@@ -60,7 +62,7 @@ typedef enum {
     OV_ESTATE = -8    /* call made in the wrong state (e.g. overlap before set_gauge) */
 } ov_status;
 
-typedef enum { OV_F64 = 0, OV_F32 = 1, OV_F16S = 2, OV_BF16S = 3 } ov_prec;
+typedef enum { OV_F64 = 0, OV_F32 = 1, OV_F16S = 2, OV_BF16S = 3, OV_DF64 = 4 } ov_prec;
 
 /* Solver report (one per call; per-rhs values up to 64 right-hand sides). */
 typedef struct {
@@ -128,8 +130,9 @@ int ov_get_eigenpairs(ov_ctx* ctx, int which, int* nev, double* vals, void* vecs
 /* Solve D(m)^dag D(m) x = b for nrhs right-hand sides to
  * ||b - A x|| / ||b|| <= tol (FP64 operator), deflated CG (Eq. 9) with the
  * stored which = 1 eigenpairs.  inner_prec selects the precision of the
- * inner operator; for inner_prec != OV_F64 the residual is recomputed in
- * FP64 (reliable updates).  precond = 1 uses the learned preconditioner in
+ * inner operator; the residual is recomputed in the accurate precision
+ * (option "hi_prec": OV_F64 or OV_DF64) whenever the inner residual has
+ * dropped by "reliable_delta" (reliable updates).  precond = 1 uses the learned preconditioner in
  * flexible CG (ov_net_train first), falling back to plain deflated CG when
  * the true residual stalls.  x may hold nothing on entry.  info may be NULL.
  * nrhs <= 16. */
@@ -216,9 +219,19 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *                    the inner-precision residual has dropped by this factor;
  *   "filter_hw" (100): Chebyshev filter degree on H_w^2 in ov_deflate(0) (Sec. V: T_100);
  *   "filter_dd" (8):  filter degree on D^dag D in ov_deflate(1);
- *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks FP64 when
- *                    tol < 1e-7 and FP32 otherwise (Gram-Schmidt and
- *                    Rayleigh-Ritz stay FP64), or an ov_prec value;
+ *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks the
+ *                    "hi_prec" precision when tol < 1e-5 and FP32 otherwise
+ *                    (Gram-Schmidt and Rayleigh-Ritz stay FP64), or an ov_prec;
+ *   "chiral" (0):     1: ov_cg_solve applies D(m)^dag D(m) on the chiral sector
+ *                    of each right-hand side as m^2 + (rho^2 - m^2/4)/rho
+ *                    (1 + chi gamma5) D(0), one sign application per iteration
+ *                    instead of two (equal up to the polynomial's error; the true
+ *                    residuals keep the full operator); every right-hand side
+ *                    must satisfy gamma5 b = chi b, else OV_EINVAL (point
+ *                    sources do).  ov_deflate(1) uses the same operator per sector;
+ *   "hi_prec" (OV_F64): precision of the accurate arithmetic in ov_cg_solve
+ *                    (true residuals, solution accumulation) and of the
+ *                    automatic ov_deflate operator: OV_F64 or OV_DF64;
  *   "proj_tc" (1):    16-bit overlap: compute eta^dag psi on the tensor cores
  *                    (0: on the CUDA cores);
  *   "net_sym" (1):    flexible CG applies the learned preconditioner as

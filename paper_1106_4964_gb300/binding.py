@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libovgb.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "overlap.h")
 
-OV_F64, OV_F32, OV_F16S, OV_BF16S = 0, 1, 2, 3
-PREC = {"f64": OV_F64, "f32": OV_F32, "f16": OV_F16S, "bf16": OV_BF16S}
+OV_F64, OV_F32, OV_F16S, OV_BF16S, OV_DF64 = 0, 1, 2, 3, 4
+PREC = {"f64": OV_F64, "f32": OV_F32, "f16": OV_F16S, "bf16": OV_BF16S, "df64": OV_DF64}
 STATUS = {0: "OV_OK", -1: "OV_EINVAL", -2: "OV_ENOMEM", -3: "OV_ECUDA", -4: "OV_ENOTCONV", -5: "OV_ESTALL",
           -6: "OV_ETIMEOUT", -7: "OV_ENAN", -8: "OV_ESTATE"}
 

@@ -175,8 +175,8 @@ int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out)
 
 static std::tuple<int, int, int> default_shape(int prec, int nrhs)
 {
-    if (nrhs == 1) return {prec == P_F64 ? 64 : 128, 1, 0};
-    const int cap = prec == P_F64 ? 8 : 16;
+    if (nrhs == 1) return {wide(prec) ? 64 : 128, 1, 0};
+    const int cap = wide(prec) ? 8 : 16;
     int by = nrhs > cap ? cap : nrhs;
     return {32, by, 0};
 }
@@ -445,6 +445,24 @@ int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double ma
     });
 }
 
+// D(m)^dag D(m) on one chiral sector (Sec. V: chiral basis, sources and
+// eigenvectors of definite chirality).  With sign^2 = 1 and gamma5 psi = chi psi,
+//   P D(m)^dag D(m) P psi = m^2 psi + (rho^2 - m^2/4)/rho (1 + chi gamma5) D(0) psi,
+// P = (1 + chi gamma5)/2: one sign application instead of two (exact up to the
+// polynomial's error delta).  dcoef: device double2 [3][R] =
+// (m^2, (rho^2 - m^2/4)/rho, chi_r (rho^2 - m^2/4)/rho), per right-hand side.
+int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, const double2* dcoef,
+                 cudaStream_t st)
+{
+    FieldDesc u;
+    OV_TRY(ws_field(c, WS_AUX0, in.prec, in.nrhs, &u));
+    return with_graph(c, 2, in, out, mass, 0, st, [&]() {
+        OV_TRY(overlap_apply_g5(c, in, u, 0.0, 0, st));  // u = D(0) in
+        FieldDesc v[3] = {in, u, u};
+        return lincomb(c, out, 3, v, nullptr, dcoef, 4, nullptr, st);
+    });
+}
+
 // Chebyshev-interpolant coefficients of x^{-1/2} on [eps, 1] at the n+1
 // Chebyshev nodes of the variable y = (2x - (1+eps))/(1-eps) (Eq. 4, Sec. V);
 // c_0 is halved so that P = sum_k c_k T_k(y).
@@ -467,7 +485,7 @@ static void cheb_coefficients(double eps, int n, std::vector<double>& c)
 
 static int check_prec(ov_ctx* c, int prec)
 {
-    if (prec < 0 || prec > 3) return set_err(c, OV_EINVAL, "unknown precision %d", prec);
+    if (prec < 0 || prec >= NPREC) return set_err(c, OV_EINVAL, "unknown precision %d", prec);
     return OV_OK;
 }
 
@@ -518,7 +536,7 @@ int ov_destroy(ov_ctx* c)
     cudaDeviceSynchronize();
     graphs_clear(c);
     net_free(c);
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < NPREC; ++p)
         if (c->gauge[p]) dev_free(c, c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p));
     for (auto& e : c->eig) eig_clear(c, e);
     for (auto& kv : c->ws) field_free(c, &kv.second);
@@ -546,11 +564,11 @@ int ov_set_gauge(ov_ctx* c, const void* U, void* stream)
     const size_t bytes = (size_t)2 * c->g.Vh * 4 * 9 * 16;
     const double* dU = nullptr;
     OV_TRY(stage_in(c, 0, U, bytes, st, &dU));
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < NPREC; ++p) {
         if (!c->gauge[p]) OV_TRY(dev_alloc(c, &c->gauge[p], (size_t)8 * c->g.Vh * gauge_link_bytes(p)));
     }
     OV_CUDA(c, cudaMemsetAsync(c->derr, 0, 2 * sizeof(unsigned), st));
-    for (int p = 0; p < 4; ++p) OV_CUDA(c, launch_pack_gauge(c->g, dU, c->gauge[p], p, p == 0 ? c->derr : nullptr, st));
+    for (int p = 0; p < NPREC; ++p) OV_CUDA(c, launch_pack_gauge(c->g, dU, c->gauge[p], p, p == 0 ? c->derr : nullptr, st));
     unsigned herr[2];
     OV_CUDA(c, cudaMemcpyAsync(herr, c->derr, sizeof herr, cudaMemcpyDeviceToHost, st));
     OV_CUDA(c, cudaStreamSynchronize(st));
@@ -852,7 +870,7 @@ int ov_project_lowmodes(ov_ctx* c, int which, const ov_field* psi, int engine, d
         OV_TRY(proj_tc_status(c, st));
     } else if (engine == 0) {
         FieldDesc eta;
-        const int pv = psi->d.prec == P_F64 ? P_F64 : (psi->d.prec == P_F32 ? P_F32 : psi->d.prec);
+        const int pv = psi->d.prec;
         OV_TRY(eig_vectors(c, which, pv, st, &eta));
         const int nblk = reduce_blocks(c->g);
         const int nparts = nblk * proj_groups(R);
@@ -882,13 +900,18 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
         if (value < 0 || value > 10000) return set_err(c, OV_EINVAL, "filter degree out of range");
         (n == "filter_hw" ? c->filter_hw : c->filter_dd) = (int)value;
     } else if (n == "eig_prec") {
-        if (value < -1 || value > 3) return set_err(c, OV_EINVAL, "eig_prec must be -1 or an ov_prec");
+        if (value < -1 || value >= NPREC) return set_err(c, OV_EINVAL, "eig_prec must be -1 or an ov_prec");
         c->eig_prec = (int)value;
     } else if (n == "proj_tc") {
         graphs_clear(c);
         c->proj_tc = value != 0;
     } else if (n == "net_sym") {
         c->net_sym = value != 0;
+    } else if (n == "chiral") {
+        c->chiral = value != 0;
+    } else if (n == "hi_prec") {
+        if (value != P_F64 && value != P_DF64) return set_err(c, OV_EINVAL, "hi_prec must be OV_F64 or OV_DF64");
+        c->hi_prec = (int)value;
     } else {
         return set_err(c, OV_EINVAL, "unknown option '%s'", name);
     }
@@ -907,9 +930,9 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
-    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant == 3 && (prec == P_F64 || by != 1)))
+    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant == 3 && (wide(prec) || by != 1)))
         return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
-    const int maxt = variant == 0 ? (prec == P_F64 ? 256 : 512) : (variant == 3 ? 128 : 256);
+    const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 ? 128 : 256);
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
     c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
@@ -930,8 +953,8 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
     // candidates: block = x sites by y right-hand sides, times the register-budget variants
     std::vector<std::tuple<int, int, int>> cand;
     for (int v = 0; v < DSLASH_VARIANTS; ++v) {
-        if (v == 3 && prec == P_F64) continue;  // staged variant: FP32 arithmetic only
-        const int maxt = v == 0 ? (prec == P_F64 ? 256 : 512) : (v == 3 ? 128 : 256);
+        if (v == 3 && wide(prec)) continue;  // staged variant: FP32 arithmetic only
+        const int maxt = v == 0 ? (wide(prec) ? 256 : 512) : (v == 3 ? 128 : 256);
         for (int x : {32, 64, 128, 256})
             for (int y = 1; y <= nrhs && y <= 16; ++y) {
                 if (v == 3 && y != 1) continue;

@@ -18,7 +18,7 @@ namespace {
 constexpr int RB_THREADS = 256;
 
 template <int P>
-using creal_t = typename std::conditional<P == P_F64, double, float>::type;
+using creal_t = typename std::conditional<P == P_F64, double, typename std::conditional<P == P_DF64, df64, float>::type>::type;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -112,7 +112,14 @@ __device__ __forceinline__ void atomic_max_pos(unsigned* a, float v) { atomicMax
 template <int P>
 __device__ __forceinline__ void store_link(char* base, int Vh, int s, const double u[12])
 {
-    if constexpr (P == P_F64) {
+    if constexpr (P == P_DF64) {
+        float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const df64 a(u[2 * k]), c(u[2 * k + 1]);
+            b[(size_t)k * Vh + s] = make_float4(a.hi, a.lo, c.hi, c.lo);
+        }
+    } else if constexpr (P == P_F64) {
         double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
         for (int k = 0; k < 6; ++k) b[(size_t)k * Vh + s] = make_double2(u[2 * k], u[2 * k + 1]);
@@ -197,7 +204,9 @@ __global__ void convert_kernel(Geom g, const char* in, const float* in_n, char* 
     const int r = blockIdx.y;
     if (idx >= 2 * g.Vh || r >= nrhs) return;
     const int p = idx >= g.Vh, s = idx - p * g.Vh;
-    using Real = typename std::conditional<PI == P_F64 || PO == P_F64, double, float>::type;
+    using Real = typename std::conditional<
+        PI == P_F64 || PO == P_F64, double,
+        typename std::conditional<PI == P_DF64 || PO == P_DF64, df64, float>::type>::type;
     Real v[24];
     constexpr size_t CI = nchunk_dev<PI>() * 16, CO = nchunk_dev<PO>() * 16;
     const size_t rp = (size_t)r * 2 + p;
@@ -332,6 +341,7 @@ cudaError_t dispatch_prec(int prec, Args&&... args)
     case P_F32: return F<P_F32>::run(args...);
     case P_F16: return F<P_F16>::run(args...);
     case P_BF16: return F<P_BF16>::run(args...);
+    case P_DF64: return F<P_DF64>::run(args...);
     }
     return cudaErrorInvalidValue;
 }
@@ -406,6 +416,7 @@ template <int PI> struct ConvertRun {
         case P_F32: return convert2<PI, P_F32>(g, in, out, st);
         case P_F16: return convert2<PI, P_F16>(g, in, out, st);
         case P_BF16: return convert2<PI, P_BF16>(g, in, out, st);
+        case P_DF64: return convert2<PI, P_DF64>(g, in, out, st);
         }
         return cudaErrorInvalidValue;
     }

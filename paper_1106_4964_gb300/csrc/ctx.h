@@ -26,6 +26,7 @@ namespace ov {
 constexpr int DSCAL_DOUBLES = 65536;
 constexpr int DSCAL_COEF = 57344;   // [0, DSCAL_COEF): coefficient blocks (double2 pairs)
 constexpr int DSCAL_CGCO = 57344;   // double2 [K][R] per-rhs coefficients
+constexpr int DSCAL_CHCO = 59392;   // double2 [3][R] coefficients of the chiral-sector operator
 constexpr int DSCAL_NORM = 61440;   // per-rhs norms
 constexpr int DSCAL_DOT = 62464;    // per-rhs dots (double2)
 constexpr int DSCAL_TMP = 64512;    // single-value scratch
@@ -33,6 +34,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
+    WS_CG_BH, WS_CG_XH,
     WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
@@ -40,7 +42,7 @@ enum Slot {
 struct EigSet {
     int nev = 0;
     std::vector<double> vals;   // host copy
-    FieldDesc vec[4] = {};      // per storage precision (F64 is the master copy)
+    FieldDesc vec[NPREC] = {};      // per storage precision (F64 is the master copy)
     double* d_sign = nullptr;   // device sign(lam_i) (which = 0)
     void* tc_rows = nullptr;    // bf16 rows of the tensor-core projection [nev][24V]
     size_t tc_bytes = 0;
@@ -57,7 +59,7 @@ struct ov_ctx {
     int device = 0;
     long long bytes = 0;
 
-    void* gauge[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* gauge[ov::NPREC] = {};
     bool have_gauge = false;
 
     double rho = 1.5, eps = 0.05, lmax = 0.0;
@@ -95,6 +97,8 @@ struct ov_ctx {
     int eig_prec = -1;            // operator precision inside deflate: -1 automatic, else ov_prec
     int proj_tc = 1;              // 16-bit overlap: low-mode projection on the tensor cores
     int net_sym = 1;              // learned preconditioner applied as (M + M^dag) / 2
+    int hi_prec = ov::P_F64;      // accurate arithmetic of the solvers: P_F64 or P_DF64
+    int chiral = 0;               // ov_cg_solve: inner operator restricted to one chiral sector
 
     // tensor-core projection buffers (proj_tc.cu)
     void* tc_b = nullptr;
@@ -140,6 +144,8 @@ int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a,
 int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
 // out = D(m)^dag D(m) in
 int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
+int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, const double2* dcoef,
+                 cudaStream_t st);
 
 // level-1 helpers (stream-ordered); results of reductions land in device memory
 int lincomb(ov_ctx* c, const FieldDesc& out, int K, const FieldDesc* x, const double2* hcoef, const double2* dcoef,

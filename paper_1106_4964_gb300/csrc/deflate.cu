@@ -20,7 +20,7 @@ constexpr int IB = 16;       // eigenvectors per pass of proj_dots
 constexpr int PD_BX = 32;    // sites per warp row
 
 template <int P>
-using dreal_t = typename std::conditional<P == P_F64, double, float>::type;
+using dreal_t = typename std::conditional<P == P_F64, double, typename std::conditional<P == P_DF64, df64, float>::type>::type;
 
 // grid (nblk, ceil(nev/IB)); block (32, BY) with y = r + nrhs * grp, BY = nrhs * G
 // partials layout [nblk * G][nev][nrhs] (double2)
@@ -28,7 +28,7 @@ template <int PV, int PS>
 __global__ void __launch_bounds__(512) proj_dots_kernel(Geom g, FieldDesc eta, int nev, FieldDesc psi, int G,
                                                         double2* partials)
 {
-    using Real = typename std::conditional<PV == P_F64 || PS == P_F64, double, float>::type;
+    using Real = dreal_t<PS>;
     constexpr size_t CV = nchunk_dev<PV>() * 16, CS = nchunk_dev<PS>() * 16;
     const int R = psi.nrhs;
     const int r = threadIdx.y % R, grp = threadIdx.y / R;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(512) proj_update_kernel(Geom g, FieldDesc eta,
                                                           const double* sg, FieldDesc psi, FieldDesc out1,
                                                           FieldDesc out2)
 {
-    using Real = typename std::conditional<PV == P_F64 || PS == P_F64, double, float>::type;
+    using Real = dreal_t<PS>;
     extern __shared__ double2 sh_c[];  // [nev][R] coefficients for out1, then [nev][R] for out2
     const int R = psi.nrhs;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -193,6 +193,7 @@ cudaError_t launch_proj_dots(const Geom& g, const FieldDesc& eta, int nev, const
     if (psi.nrhs * groups_for(psi.nrhs) * PD_BX > 512) return cudaErrorInvalidValue;
     int pv = eta.prec, ps = psi.prec;
     if (pv == P_F64 && ps == P_F64) return dots2<P_F64, P_F64>(g, eta, nev, psi, partials, nblk, st);
+    if (pv == P_DF64 && ps == P_DF64) return dots2<P_DF64, P_DF64>(g, eta, nev, psi, partials, nblk, st);
     if (pv == P_F32 && ps == P_F32) return dots2<P_F32, P_F32>(g, eta, nev, psi, partials, nblk, st);
     if (pv == P_F16 && ps == P_F32) return dots2<P_F16, P_F32>(g, eta, nev, psi, partials, nblk, st);
     if (pv == P_BF16 && ps == P_F32) return dots2<P_BF16, P_F32>(g, eta, nev, psi, partials, nblk, st);
@@ -213,6 +214,7 @@ cudaError_t launch_proj_update(const Geom& g, const FieldDesc& eta, int nev, con
     if (psi.nrhs > 16) return cudaErrorInvalidValue;
     int pv = eta.prec, ps = psi.prec;
     if (pv == P_F64 && ps == P_F64) return update2<P_F64, P_F64>(g, eta, nev, c, s, psi, out1, out2, st);
+    if (pv == P_DF64 && ps == P_DF64) return update2<P_DF64, P_DF64>(g, eta, nev, c, s, psi, out1, out2, st);
     if (pv == P_F32 && ps == P_F32) return update2<P_F32, P_F32>(g, eta, nev, c, s, psi, out1, out2, st);
     if (pv == P_F16 && ps == P_F32) return update2<P_F16, P_F32>(g, eta, nev, c, s, psi, out1, out2, st);
     if (pv == P_BF16 && ps == P_F32) return update2<P_BF16, P_F32>(g, eta, nev, c, s, psi, out1, out2, st);

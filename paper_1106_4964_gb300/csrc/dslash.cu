@@ -32,7 +32,9 @@ namespace ov {
 namespace {
 
 template <int SP>
-using real_t = typename std::conditional<SP == P_F64, double, float>::type;
+using real_t = typename std::conditional<SP == P_F64, double, typename std::conditional<SP == P_DF64, df64, float>::type>::type;
+template <int SP>
+constexpr bool wide_dev = SP == P_F64 || SP == P_DF64;
 
 template <int MU, int S, typename Real>
 __device__ __forceinline__ void project(const Real v[24], Real h[12])
@@ -157,8 +159,8 @@ __device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int 
 // the registers so that more warps are resident to hide load latency.
 template <int SP, int VAR>
 struct Bounds {
-    static constexpr int maxt = VAR == 0 ? (SP == P_F64 ? 256 : 512) : 256;
-    static constexpr int minb = VAR == 0 ? 1 : (SP == P_F64 ? VAR + 1 : VAR + 2);
+    static constexpr int maxt = VAR == 0 ? (wide_dev<SP> ? 256 : 512) : 256;
+    static constexpr int minb = VAR == 0 ? 1 : (wide_dev<SP> ? VAR + 1 : VAR + 2);
 };
 
 template <int SP, int GP, int NY, int VAR>
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) 
     const Geom& g = A.g;
     if (s >= g.Vh || r >= A.nrhs) return;
 
-    constexpr size_t CH = (SP == P_F64 ? 12 : (SP == P_F32 ? 6 : 3)) * 16;
+    constexpr size_t CH = nchunk_dev<SP>() * 16;
     const size_t par_bytes = CH * g.Vh;
     const int q = 1 - p;
     const char* in_q = A.in + ((size_t)r * 2 + q) * par_bytes;
@@ -207,7 +209,7 @@ __device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int 
 {
     using Real = real_t<SP>;
     const Geom& g = A.g;
-    constexpr size_t CH = (SP == P_F64 ? 12 : (SP == P_F32 ? 6 : 3)) * 16;
+    constexpr size_t CH = nchunk_dev<SP>() * 16;
     const size_t par_bytes = CH * g.Vh;
     const size_t off = ((size_t)r * 2 + p) * par_bytes;
     const size_t noff = ((size_t)r * 2 + p) * g.Vh;
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
 template <int SP, int GP>
 cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
 {
-    if constexpr (SP == P_F64) {
+    if constexpr (wide_dev<SP>) {
         return cudaErrorInvalidValue;
     } else {
         if (block.y != 1 || block.x > 128) return cudaErrorInvalidValue;
@@ -484,10 +486,11 @@ cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 bloc
 
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st)
 {
-    if (bx <= 0 || by <= 0 || bx * by > (sp == P_F64 ? 256 : 512)) return cudaErrorInvalidValue;
+    if (bx <= 0 || by <= 0 || bx * by > (wide(sp) ? 256 : 512)) return cudaErrorInvalidValue;
     dim3 block(bx, by);
     dim3 grid(2 * ((A.g.Vh + bx - 1) / bx), (A.nrhs + by - 1) / by);
     if (sp == P_F64 && gp == P_F64) return launch_ny<P_F64, P_F64>(A, ny, var, grid, block, st);
+    if (sp == P_DF64 && gp == P_DF64) return launch_ny<P_DF64, P_DF64>(A, ny, var, grid, block, st);
     if (sp == P_F32 && gp == P_F32) return launch_ny<P_F32, P_F32>(A, ny, var, grid, block, st);
     if (sp == P_F16 && gp == P_F16) return launch_ny<P_F16, P_F16>(A, ny, var, grid, block, st);
     if (sp == P_BF16 && gp == P_BF16) return launch_ny<P_BF16, P_BF16>(A, ny, var, grid, block, st);

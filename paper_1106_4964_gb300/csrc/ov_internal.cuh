@@ -24,20 +24,86 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include <string>
 
 namespace ov {
 
-enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+// P_DF64: FP64-class "double-float" format: every real is an unevaluated sum
+// hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2, about 48 significand bits),
+// 8 bytes per real like FP64, computed on the FP32 pipes with error-free
+// transformations.  GB300's FP64 units are a small fraction of its FP32
+// throughput, so this is the fast form of the FP64-accurate operator.
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3, P_DF64 = 4 };
+constexpr int NPREC = 5;
 
-inline int spinor_chunks(int prec) { return prec == P_F64 ? 12 : (prec == P_F32 ? 6 : 3); }
+inline bool wide(int prec) { return prec == P_F64 || prec == P_DF64; }
+inline int spinor_chunks(int prec) { return wide(prec) ? 12 : (prec == P_F32 ? 6 : 3); }
 inline bool has_norm(int prec) { return prec == P_F16 || prec == P_BF16; }
 inline size_t spinor_site_bytes(int prec) { return (size_t)spinor_chunks(prec) * 16; }
-inline size_t gauge_link_bytes(int prec) { return prec == P_F64 ? 96 : (prec == P_F32 ? 48 : 24); }
+inline size_t gauge_link_bytes(int prec) { return wide(prec) ? 96 : (prec == P_F32 ? 48 : 24); }
 template <int P>
-__host__ __device__ constexpr size_t gauge_link_bytes_dev() { return P == P_F64 ? 96 : (P == P_F32 ? 48 : 24); }
+__host__ __device__ constexpr size_t gauge_link_bytes_dev()
+{
+    return (P == P_F64 || P == P_DF64) ? 96 : (P == P_F32 ? 48 : 24);
+}
 template <int P>
-__host__ __device__ constexpr int nchunk_dev() { return P == P_F64 ? 12 : (P == P_F32 ? 6 : 3); }
+__host__ __device__ constexpr int nchunk_dev() { return (P == P_F64 || P == P_DF64) ? 12 : (P == P_F32 ? 6 : 3); }
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (Dekker / Knuth error-free transformations)
+// ---------------------------------------------------------------------------
+struct df64 {
+    float hi, lo;
+    df64() = default;
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr df64(float f) : hi(f), lo(0.f) {}
+    __host__ __device__ constexpr df64(int i) : hi((float)i), lo(0.f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ df64 df_renorm(float s, float e)
+{
+    const float hi = s + e;
+    return df64(hi, e - (hi - s));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+{
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);  // two-sum error
+    e += a.lo + b.lo;
+    return df_renorm(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);  // two-product error
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_renorm(p, e);
+}
+__device__ __forceinline__ df64 operator*(float a, df64 b)
+{
+    const float p = a * b.hi;
+    float e = fmaf(a, b.hi, -p);
+    e = fmaf(a, b.lo, e);
+    return df_renorm(p, e);
+}
+__device__ __forceinline__ df64 operator*(int s, df64 b)
+{
+    if (s == 1) return b;
+    if (s == -1) return -b;
+    return (float)s * b;
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
 struct Geom {
     int L[4];   // Lx, Ly, Lz, Lt
@@ -111,11 +177,36 @@ template <> struct Half<P_BF16> {
 // spinor load / store: v[24] = (spin, colour, re/im)
 // `base` points at chunk 0 of one (rhs, parity); `nrm` at its norm array.
 // ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R from_df(df64 a)
+{
+    if constexpr (std::is_same<R, df64>::value)
+        return a;
+    else
+        return (R)a;
+}
+template <typename R>
+__device__ __forceinline__ df64 to_df(R v)
+{
+    if constexpr (std::is_same<R, df64>::value)
+        return v;
+    else
+        return df64(v);
+}
+
 template <int P, typename Real>
 __device__ __forceinline__ void load_spinor(const char* __restrict__ base, const float* __restrict__ nrm,
                                             int Vh, int s, Real v[24])
 {
-    if constexpr (P == P_F64) {
+    if constexpr (P == P_DF64) {
+        const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 t = __ldg(b + (size_t)k * Vh + s);
+            v[2 * k] = from_df<Real>(df64(t.x, t.y));
+            v[2 * k + 1] = from_df<Real>(df64(t.z, t.w));
+        }
+    } else if constexpr (P == P_F64) {
         const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -157,7 +248,14 @@ template <int P, typename Real>
 __device__ __forceinline__ void store_spinor(char* __restrict__ base, float* __restrict__ nrm, int Vh, int s,
                                              const Real v[24])
 {
-    if constexpr (P == P_F64) {
+    if constexpr (P == P_DF64) {
+        float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const df64 a = to_df<Real>(v[2 * k]), c = to_df<Real>(v[2 * k + 1]);
+            b[(size_t)k * Vh + s] = make_float4(a.hi, a.lo, c.hi, c.lo);
+        }
+    } else if constexpr (P == P_F64) {
         double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) b[(size_t)k * Vh + s] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
@@ -193,7 +291,15 @@ __device__ __forceinline__ void store_spinor(char* __restrict__ base, float* __r
 template <int P, typename Real>
 __device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh, int s, Real u[18])
 {
-    if constexpr (P == P_F64) {
+    if constexpr (P == P_DF64) {
+        const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 t = __ldg(b + (size_t)k * Vh + s);
+            u[2 * k] = from_df<Real>(df64(t.x, t.y));
+            u[2 * k + 1] = from_df<Real>(df64(t.z, t.w));
+        }
+    } else if constexpr (P == P_F64) {
         const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {

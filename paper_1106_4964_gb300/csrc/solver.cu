@@ -373,7 +373,7 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
     int Keff = K;
     if (K > 0) {
         const double y0 = (bmax + acut) / (bmax - acut);
-        const double limit = W.tmp[0].prec == P_F64 ? 1e12 : 1e4;
+        const double limit = W.tmp[0].prec == P_F64 ? 1e12 : (W.tmp[0].prec == P_DF64 ? 1e10 : 1e4);
         const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
         Keff = std::max(2, std::min(K, kmax));
     }
@@ -534,7 +534,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const int kkeep = std::min(m - 1, ns + (m - ns) / 3);
     // operator precision: FP64 when the eigen-residual target needs it; an FP32 filter (FP64
     // Gram-Schmidt and Rayleigh-Ritz) when tol >= 1e-7, or as set by ov_set_option("eig_prec")
-    const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : P_F64);
+    const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : c->hi_prec);
 
     LanczosWork W{};
     FieldDesc outv{}, tsa{}, tsb{}, ta{};
@@ -605,13 +605,17 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         rscale = lm;
         K = c->filter_hw;
     } else {
+        // D^dag D, or with the "chiral" option its one-sign form on the sector being solved
+        const double2* dchi = (const double2*)(c->dscal + DSCAL_CHCO);
+        Awork = [&, dchi](const FieldDesc& in, const FieldDesc& out) -> int {
+            return c->chiral ? chiral_apply(c, in, out, 0.0, dchi, st) : normal_apply(c, in, out, 0.0, st);
+        };
         A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            if (oprec == P_F64) return normal_apply(c, in, out, 0.0, st);
+            if (oprec == P_F64) return Awork(in, out);
             OV_TRY(convert(c, in, tsa, st));
-            OV_TRY(normal_apply(c, tsa, tsb, 0.0, st));
+            OV_TRY(Awork(tsa, tsb));
             return convert(c, tsb, out, st);
         };
-        Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int { return normal_apply(c, in, out, 0.0, st); };
         R = A;
         bmax = 4.0 * c->rho * c->rho * 1.01;
         rscale = bmax;
@@ -621,6 +625,10 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     double worst = 0;
     for (int s = 0; s < nsec; ++s) {
         const int chi = which == 0 ? 0 : (s == 0 ? +1 : -1);
+        if (which == 1 && c->chiral) {
+            const double2 hc[3] = {make_double2(0, 0), make_double2(c->rho, 0), make_double2(chi * c->rho, 0)};
+            DF_TRY(to_dev(c, hc, c->dscal + DSCAL_CHCO, sizeof hc, st));
+        }
         std::vector<double> v;
         double mr = 0;
         DF_TRY(trlan(c, A, Awork, R, K, bmax, ns, m, kkeep, tol, rscale, chi, 4242ull + 17 * which + s, W, v,
@@ -646,20 +654,28 @@ int net_apply_precond(ov_ctx* c, const FieldDesc& r, const FieldDesc& z, cudaStr
 bool net_ready(const ov_ctx* c);
 int net_record_pair(ov_ctx* c, const FieldDesc& r64, const FieldDesc& x64, cudaStream_t st);
 
-int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
-            int inner_prec, ov_solve_info* info, cudaStream_t st)
+int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mass, double tol, int max_iter,
+            int precond, int inner_prec, ov_solve_info* info, cudaStream_t st)
 {
     auto t0 = std::chrono::steady_clock::now();
-    const int R = b.nrhs;
+    const int R = b_in.nrhs;
     const int Ps = inner_prec;
-    const bool sloppy = Ps != P_F64;
+    // accurate arithmetic (true residuals, the accumulated solution): FP64 or double-float
+    const int Ph = c->hi_prec;
+    const bool sloppy = Ps != Ph;
     if (precond && !net_ready(c)) return set_err(c, OV_ESTATE, "cg: learned preconditioner requested but not trained");
     EigSet& X = c->eig[1];
     const int nd = X.nev;
+    FieldDesc b = b_in, x = x_out;
+    if (b_in.prec != Ph) {
+        OV_TRY(ws_field(c, WS_CG_BH, Ph, R, &b));
+        OV_TRY(ws_field(c, WS_CG_XH, Ph, R, &x));
+        OV_TRY(convert(c, b_in, b, st));
+    }
     FieldDesc r, t, rs, ps, qs, xs, xt, zs, rold;
-    OV_TRY(ws_field(c, WS_CG_R, P_F64, R, &r));
-    OV_TRY(ws_field(c, WS_CG_T, P_F64, R, &t));
-    OV_TRY(ws_field(c, WS_CG_U, P_F64, R, &xt));
+    OV_TRY(ws_field(c, WS_CG_R, Ph, R, &r));
+    OV_TRY(ws_field(c, WS_CG_T, Ph, R, &t));
+    OV_TRY(ws_field(c, WS_CG_U, Ph, R, &xt));
     if (sloppy) {
         OV_TRY(ws_field(c, WS_CG_RS, Ps, R, &rs));
     } else {
@@ -691,7 +707,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, doub
     if ((size_t)2 * nd * R * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "cg: nev * nrhs too large");
     FieldDesc xi64{}, xis{};
     if (nd) {
-        OV_TRY(eig_vectors(c, 1, P_F64, st, &xi64));
+        OV_TRY(eig_vectors(c, 1, Ph, st, &xi64));
         OV_TRY(eig_vectors(c, 1, Ps, st, &xis));
     }
     auto project = [&](const FieldDesc& xiv, const FieldDesc& v) -> int {
@@ -704,6 +720,33 @@ int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, doub
     OV_TRY(to_host(c, ddt, hb.data(), R * sizeof(double2), st));
     std::vector<double> bn(R);
     for (int q = 0; q < R; ++q) bn[q] = hb[q].x > 0 ? std::sqrt(hb[q].x) : 1.0;
+
+    // chiral-sector inner operator: every right-hand side must have definite chirality
+    // (b^dag gamma5 b = +-|b|^2); the true residuals keep the full D^dag D
+    const double2* dch = (const double2*)(c->dscal + DSCAL_CHCO);
+    if (c->chiral) {
+        FieldDesc v1[1] = {b};
+        double2 one[1] = {make_double2(1, 0)};
+        OV_TRY(lincomb(c, t, 1, v1, one, nullptr, 1, nullptr, st));  // t = gamma5 b
+        OV_TRY(dot(c, b, t, ddt, st));
+        std::vector<double2> hg(R);
+        OV_TRY(to_host(c, ddt, hg.data(), R * sizeof(double2), st));
+        const double cm = (c->rho * c->rho - 0.25 * mass * mass) / c->rho;
+        std::vector<double2> hc(3 * R);
+        for (int q = 0; q < R; ++q) {
+            const double n2 = bn[q] * bn[q];
+            if (!(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
+                return set_err(c, OV_EINVAL, "cg: chiral mode needs right-hand sides of definite chirality (rhs %d)", q);
+            const double chi = hg[q].x > 0 ? 1.0 : -1.0;
+            hc[q] = make_double2(mass * mass, 0);
+            hc[R + q] = make_double2(cm, 0);
+            hc[2 * R + q] = make_double2(chi * cm, 0);
+        }
+        OV_TRY(to_dev(c, hc.data(), (void*)dch, hc.size() * sizeof(double2), st));
+    }
+    auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+        return c->chiral ? chiral_apply(c, in, out, mass, dch, st) : normal_apply(c, in, out, mass, st);
+    };
 
     std::vector<double> rr(R), rr_new(R), rmax(R), res(R, 1.0), rz(R);
     std::vector<char> done(R, 0);
@@ -791,7 +834,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, doub
         int since = 0;
         std::vector<double2> co(2 * R);
         while (iters < max_iter) {
-            OV_TRY(normal_apply(c, ps, qs, mass, st));
+            OV_TRY(inner_apply(ps, qs));
             OV_TRY(dot(c, ps, qs, ddt, st));
             std::vector<double2> h(R);
             OV_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
@@ -901,6 +944,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, doub
             OV_TRY(refresh(all_done));
         }
     }
+    if (x.data != x_out.data) OV_TRY(convert(c, x, x_out, st));
     OV_CUDA(c, cudaStreamSynchronize(st));
     if (info) {
         memset(info, 0, sizeof *info);

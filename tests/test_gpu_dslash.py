@@ -21,7 +21,7 @@ def _gpu():
 
 
 @pytest.mark.parametrize("dims", DIMS)
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "df64"])
 def test_dslash_parity(dims, prec):
     from paper_1106_4964_gb300 import Context
 
@@ -40,7 +40,7 @@ def test_dslash_parity(dims, prec):
     assert err <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 12), ("f16", 5), ("f64", 12)])
+@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 12), ("f16", 5), ("f64", 12), ("df64", 7)])
 def test_multi_rhs(prec, nrhs):
     from paper_1106_4964_gb300 import Context
 
@@ -121,7 +121,7 @@ def big():
     return dims, U, psi
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64", "f16"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "f16", "df64"])
 def test_full_size_sampled_sites(big, prec):
     """24^3 x 64 (the benchmark workload), internal-field launch as timed by bench.py;
     256 sampled output sites against the oracle computed site by site."""
@@ -143,7 +143,7 @@ def test_full_size_sampled_sites(big, prec):
     assert rel(got[sites], ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6), ("f16", 2e-3)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6), ("f16", 2e-3), ("df64", 1e-13)])
 def test_field_dot(prec, tol):
     """FP64-accumulated scalar products of internal fields (Sec. III) against numpy."""
     from paper_1106_4964_gb300 import Context

@@ -37,9 +37,13 @@ def test_lambda_max_estimate(cfg1):
     assert abs(lm / cfg1["lmax"] - 1) < 1e-3
 
 
-def test_deflate_hw_modes(cfg1):
+@pytest.mark.parametrize("hi", ["f64", "df64"])
+def test_deflate_hw_modes(cfg1, hi):
+    from paper_1106_4964_gb300 import PREC
+
     cf = cfg1
     ctx = make_ctx(cf)
+    ctx.set_option("hi_prec", PREC[hi])  # filter operator of the tol < 1e-5 eigensolve
     nev = 12
     ctx.deflate(0, nev, 1e-10)
     vals, vecs = ctx.get_eigenpairs(0)
@@ -70,11 +74,15 @@ def test_deflate_normal_modes_small():
         assert np.linalg.norm(r) <= 1e-8 * mu[-1]
 
 
-@pytest.mark.parametrize("inner", ["f64", "f32"])
-def test_cg_config1(cfg1, inner):
-    """Config 1: CG on D_ov^dag D_ov x = b to 1e-10 (true FP64 residual by the oracle)."""
+@pytest.mark.parametrize("inner,hi", [("f64", "f64"), ("f32", "f64"), ("f32", "df64"), ("df64", "df64")])
+def test_cg_config1(cfg1, inner, hi):
+    """Config 1: CG on D_ov^dag D_ov x = b to 1e-10 (true FP64 residual by the oracle), with the
+    accurate arithmetic in FP64 or in double-float."""
+    from paper_1106_4964_gb300 import PREC
+
     cf = cfg1
     ctx = make_ctx(cf)
+    ctx.set_option("hi_prec", PREC[hi])
     b = synth.gaussian_spinor(cf["dims"], 2)
     x = torch.empty_like(dev(b))
     info = ctx.cg_solve(dev(b), x, mass=0.0, tol=1e-10, max_iter=2000, inner_prec=inner)
@@ -82,7 +90,8 @@ def test_cg_config1(cfg1, inner):
     Ax = oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], xs, cf["ev"],
                                cf["eta"])
     res = rel(Ax, b)
-    print(f"cg config1 inner={inner}: iters {info['iterations']} updates {info['reliable_updates']} res {res:.2e}")
+    print(f"cg config1 inner={inner} hi={hi}: iters {info['iterations']} updates {info['reliable_updates']} "
+          f"res {res:.2e}")
     assert res <= 1e-10
     assert info["true_residual"][0] <= 1e-10
 
@@ -115,3 +124,57 @@ def test_cg_matches_oracle_solution():
     assert res <= 1e-12
     # both solutions satisfy the same system to 1e-12; their difference is bounded by kappa * 1e-12
     assert rel(host(x), xo) < 1e-8
+
+
+def test_cg_chiral_sector(cfg1):
+    """Point sources have definite chirality: the chiral-sector inner operator (one sign
+    application per iteration) converges to the same FP64 true residual of the full D^dag D."""
+    cf = cfg1
+    ctx = make_ctx(cf)
+    b = synth.point_sources(cf["dims"])[[0, 4, 7, 11]]  # spins 0, 1 (chirality +) and 2, 3 (-)
+    x = torch.empty_like(dev(b))
+    n0 = ctx.dslash_count()
+    full = ctx.cg_solve(dev(b), x, mass=0.05, tol=1e-10, max_iter=2000, inner_prec="f32")
+    d_full = ctx.dslash_count() - n0
+    ctx.set_option("chiral", 1)
+    n0 = ctx.dslash_count()
+    chir = ctx.cg_solve(dev(b), x, mass=0.05, tol=1e-10, max_iter=2000, inner_prec="f32")
+    d_chir = ctx.dslash_count() - n0
+    xs = host(x)
+    for r in range(len(b)):
+        Ax = oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.05, cf["lmax"], cf["eps"], cf["c"], xs[r],
+                                   cf["ev"], cf["eta"])
+        assert rel(Ax, b[r]) <= 1e-10
+    print(f"chiral cg: iterations {chir['iterations']} (full {full['iterations']}), dslash {d_chir} vs {d_full}")
+    assert chir["iterations"] <= full["iterations"] + 5
+    assert d_chir < 0.7 * d_full
+
+
+def test_cg_chiral_rejects_mixed_chirality(cfg1):
+    from paper_1106_4964_gb300 import OverlapError
+
+    cf = cfg1
+    ctx = make_ctx(cf)
+    ctx.set_option("chiral", 1)
+    b = synth.gaussian_spinor(cf["dims"], 5)
+    with pytest.raises(OverlapError):
+        ctx.cg_solve(dev(b), torch.empty_like(dev(b)), mass=0.05, tol=1e-10, max_iter=10)
+
+
+def test_deflate_normal_modes_chiral():
+    """D^dag D modes found with the one-sign chiral-sector operator agree with the dense
+    spectrum of the full operator to the polynomial's accuracy."""
+    cf = setup((2, 2, 2, 4), 0.7, 4, 0.02, 80)
+    ctx = make_ctx(cf)
+    ctx.set_option("chiral", 1)
+    V = oracle.volume(cf["dims"])
+    A = dense(lambda v: oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], v,
+                                              cf["ev"], cf["eta"]), V)
+    mu = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
+    nev = 6
+    ctx.deflate(1, nev, 1e-9)
+    vals, vecs = ctx.get_eigenpairs(1)
+    assert np.allclose(np.sort(vals), mu[:nev], atol=1e-8 * mu[-1])
+    for i in range(nev):
+        r = A @ vecs[i] - vals[i] * vecs[i]
+        assert np.linalg.norm(r) <= 1e-8 * mu[-1]

@@ -207,6 +207,25 @@ def test_normal_operator_identity(dense_overlap):
     assert np.abs(D.conj().T - g5 @ D @ g5).max() < 1e-10
 
 
+@pytest.mark.parametrize("m", [0.0, 0.07])
+def test_chiral_sector_normal_operator(dense_overlap, m):
+    """On a chiral sector (gamma5 = chi) the normal operator needs one sign application:
+    P D(m)^dag D(m) P = m^2 P + (rho^2 - m^2/4)/rho (1 + chi gamma5) D(0) P, P = (1 + chi gamma5)/2,
+    a consequence of sign^2 = 1 (the chiral basis of Sec. V).  The oracle's two-sign D^dag D
+    and its one-sign D(0) are compared on random vectors of each sector."""
+    dims, U, D, (lmax, eps, c, ev, eta) = dense_overlap
+    psi = synth.gaussian_spinor(dims, 8)[0]
+    for chi in (+1, -1):
+        ph = psi.copy()
+        ph[..., (2, 3) if chi > 0 else (0, 1), :] = 0  # project onto the sector
+        ph = ph.reshape(-1)
+        lhs = oracle.overlap_normal(dims, ABC, U, RHO, m, lmax, eps, c, ph, ev, eta)
+        u = oracle.overlap(dims, ABC, U, RHO, 0.0, lmax, eps, c, ph, ev, eta)
+        cm = (RHO ** 2 - m * m / 4) / RHO
+        rhs = m * m * ph + cm * (u + chi * oracle.gamma5(u).reshape(-1))
+        assert rel(rhs, lhs) < 1e-12
+
+
 def test_massive_overlap_eq8(dense_overlap):
     """D(m) = rho D + m (1 - D/2): affine in m with the massless operator (D = D(0)/rho)."""
     dims, U, D, (lmax, eps, c, ev, eta) = dense_overlap
