@@ -161,6 +161,19 @@ int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cuda
 
 int gauge_prec_for(int prec) { return prec; }
 
+// Flags set by kernels whose bounded waits ran out (derr[2]); read and cleared.
+int check_kernel_flags(ov_ctx* c, cudaStream_t st)
+{
+    unsigned f = 0;
+    OV_CUDA(c, cudaMemcpyAsync(&f, c->derr + 2, sizeof f, cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    if (f) {
+        OV_CUDA(c, cudaMemsetAsync(c->derr + 2, 0, sizeof f, st));
+        return set_err(c, OV_ETIMEOUT, "a staged dslash launch timed out waiting for its copies");
+    }
+    return OV_OK;
+}
+
 int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out)
 {
     EigSet& E = c->eig[which];
@@ -188,6 +201,7 @@ int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a,
     DslashArgs A;
     memset(&A, 0, sizeof A);
     A.g = c->g;
+    A.err = c->derr + 2;
     A.gauge = (const char*)c->gauge[gprec];
     A.in = in.data;
     A.in_n = in.norm;
@@ -526,6 +540,10 @@ int ov_create(ov_ctx** ctx, const int dims[4], const double bc_phase[4])
         return OV_ENOMEM;
     }
     c->derr = (unsigned*)p;
+    if (cudaMemset(c->derr, 0, 64) != cudaSuccess) {
+        ov_destroy(c);
+        return OV_ECUDA;
+    }
     *ctx = c;
     return OV_OK;
 }
@@ -612,7 +630,8 @@ static int apply_canonical(ov_ctx* c, const void* in, void* out, double m, int n
     else
         OV_TRY(dslash_apply(c, fi, fo, 4.0 + m, -0.5, kind == 1, 0, 0, nullptr, nullptr, st));
     OV_CUDA(c, launch_unpack(c->g, fo, dout, 0, st));
-    return stage_out_finish(c, out, dout, bytes, st);
+    OV_TRY(stage_out_finish(c, out, dout, bytes, st));
+    return check_kernel_flags(c, st);
 }
 
 int ov_apply_dslash(ov_ctx* c, const void* in, void* out, double m, int nrhs, int prec, void* stream)
@@ -930,7 +949,7 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
-    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant == 3 && (wide(prec) || by != 1)))
+    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant >= 3 && (wide(prec) || by != 1)))
         return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
     const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 ? 128 : 256);
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
@@ -953,7 +972,11 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
     // candidates: block = x sites by y right-hand sides, times the register-budget variants
     std::vector<std::tuple<int, int, int>> cand;
     for (int v = 0; v < DSLASH_VARIANTS; ++v) {
-        if (v == 3 && wide(prec)) continue;  // staged variant: FP32 arithmetic only
+        if (v >= 3 && wide(prec)) continue;  // staged variants: FP32 arithmetic only
+        if (v == 4) {                        // bulk-copy staging: fixed 128-site blocks
+            cand.push_back(std::make_tuple(128, 1, 4));
+            continue;
+        }
         const int maxt = v == 0 ? (wide(prec) ? 256 : 512) : (v == 3 ? 128 : 256);
         for (int x : {32, 64, 128, 256})
             for (int y = 1; y <= nrhs && y <= 16; ++y) {

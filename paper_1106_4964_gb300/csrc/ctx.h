@@ -136,6 +136,7 @@ int stage_in(ov_ctx* c, int which, const void* src, size_t bytes, cudaStream_t s
 int stage_out_buffer(ov_ctx* c, int which, void* dst, size_t bytes, double** dev);
 int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cudaStream_t st);
 int gauge_prec_for(int prec);
+int check_kernel_flags(ov_ctx* c, cudaStream_t st);
 int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out);
 
 // operators on internal fields

@@ -456,6 +456,262 @@ cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cu
     }
 }
 
+// ---------------------------------------------------------------------------
+// Variant 4 (FP32 arithmetic, FP32 or 16-bit storage): neighbour spinors
+// staged in shared memory by the bulk-copy engine (1-D TMA).  A block owns
+// TB consecutive checkerboard sites [s0, s0 + TB) of one parity and one
+// right-hand side; the neighbours of the other parity lie in five index
+// ranges, [s0 - Lxh - 1, s0 + TB + Lxh + 1) for the x and y hops and the
+// ranges shifted by +-Lxh Ly (z hops) and +-Lxh Ly Lz (t hops).  Thread 0
+// issues one cp.async.bulk per (range, chunk) plus the per-site scales of
+// 16-bit storage, all completing on one mbarrier; a hop whose neighbour lies
+// outside its range (lattice wrap-around, clipped array ends) reads global
+// memory instead.  Links have no reuse within a parity and stay plain loads.
+// Blocks are ordered (site block, parity, rhs) with the rhs fastest, so the
+// right-hand sides of one site block read the same links back to back (L2).
+// ---------------------------------------------------------------------------
+constexpr int TMA_TB = 128;                 // sites per block
+constexpr long long TMA_SPIN = 1ll << 22;   // bounded mbarrier wait
+
+struct TmaPlan {
+    int cap[5];        // slots per range
+    int spin_off[5];   // byte offsets of the spinor slots
+    int nrm_off[5];    // byte offsets of the scale slots (16-bit storage)
+    int bytes;         // dynamic shared memory
+};
+
+__host__ __device__ inline TmaPlan tma_plan(int Lxh, int nch, bool nrm)
+{
+    TmaPlan P;
+    int off = 16;  // the mbarrier
+    for (int j = 0; j < 5; ++j) {
+        P.cap[j] = j == 0 ? TMA_TB + 2 * Lxh + 2 : TMA_TB;
+        P.spin_off[j] = off;
+        off += nch * P.cap[j] * 16;
+    }
+    for (int j = 0; j < 5; ++j) {
+        P.nrm_off[j] = off;
+        if (nrm) off += ((P.cap[j] + 8) * 4 + 15) & ~15;
+    }
+    P.bytes = off;
+    return P;
+}
+
+__device__ __forceinline__ void tma_mbar_init(uint64_t* b)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_expect(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool tma_wait(uint64_t* b)
+{
+    for (long long i = 0; i < TMA_SPIN; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(b))
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// spinor of slot i of a staged range (chunk-major, `cap` slots per chunk)
+template <int SP>
+__device__ __forceinline__ void load_spinor_smem(const uint8_t* base, const float* nrm, int cap, int i, float v[24])
+{
+    if constexpr (SP == P_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(base + ((size_t)k * cap + i) * 16);
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = a.z;
+            v[4 * k + 3] = a.w;
+        }
+    } else {
+        const float n = *nrm;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 a = *reinterpret_cast<const uint4*>(base + ((size_t)k * cap + i) * 16);
+            const float2 a0 = Half<SP>::to2(a.x), a1 = Half<SP>::to2(a.y), a2 = Half<SP>::to2(a.z),
+                         a3 = Half<SP>::to2(a.w);
+            v[8 * k + 0] = a0.x * n;
+            v[8 * k + 1] = a0.y * n;
+            v[8 * k + 2] = a1.x * n;
+            v[8 * k + 3] = a1.y * n;
+            v[8 * k + 4] = a2.x * n;
+            v[8 * k + 5] = a2.y * n;
+            v[8 * k + 6] = a3.x * n;
+            v[8 * k + 7] = a3.y * n;
+        }
+    }
+}
+
+struct TmaRange {
+    int a, n, na;  // first staged index, count, first staged scale index
+};
+
+template <int SP, int GP, int MU, int S>
+__device__ __forceinline__ void hop_tma(const DslashArgs& A, const uint8_t* sm, const TmaPlan& P, const TmaRange& rg,
+                                        int j, const char* in_q, const float* inn_q, int p, int s, int sn, bool cross,
+                                        float acc[24])
+{
+    float v[24];
+    const int i = sn - rg.a;
+    if ((unsigned)i < (unsigned)rg.n) {
+        const float* nrm = nullptr;
+        if constexpr (SP == P_F16 || SP == P_BF16)
+            nrm = reinterpret_cast<const float*>(sm + P.nrm_off[j]) + (sn - rg.na);
+        load_spinor_smem<SP>(sm + P.spin_off[j], nrm, P.cap[j], i, v);
+    } else {
+        load_spinor<SP, float>(in_q, inn_q, A.g.Vh, sn, v);
+    }
+    float h[12];
+    project<MU, S, float>(v, h);
+    if (cross) {
+        const float ph = (float)A.g.bc[MU];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) h[k] *= ph;
+    }
+    const int lpar = S > 0 ? p : 1 - p;
+    const int ls = S > 0 ? s : sn;
+    const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
+    float u[18];
+    load_link<GP, float>(lb, A.g.Vh, ls, u);
+    float chi[12];
+    link_mul<S, float>(u, h, chi);
+    accumulate<MU, S, float>(acc, chi);
+}
+
+template <int SP, int GP, int NY>
+__global__ void __launch_bounds__(TMA_TB) dslash_tma_kernel(DslashArgs A)
+{
+    extern __shared__ __align__(128) uint8_t sm[];
+    constexpr int SCH = nchunk_dev<SP>();
+    constexpr bool NRM = SP == P_F16 || SP == P_BF16;
+    const Geom& g = A.g;
+    const int r = blockIdx.x % A.nrhs;
+    const int rest = blockIdx.x / A.nrhs;
+    const int p = rest & 1, q = 1 - p;
+    const int s0 = (rest >> 1) * TMA_TB;
+    const char* in_q = A.in + ((size_t)r * 2 + q) * SCH * 16 * g.Vh;
+    const float* inn_q = NRM ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
+    const TmaPlan P = tma_plan(g.Lxh, SCH, NRM);
+    const int PL = g.Lxh * g.L[1], VL = PL * g.L[2];
+    const int lo[5] = {s0 - g.Lxh - 1, s0 + PL, s0 - PL, s0 + VL, s0 - VL};
+    TmaRange rg[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int a = lo[j] < 0 ? 0 : lo[j];
+        const int e = lo[j] + P.cap[j] > g.Vh ? g.Vh : lo[j] + P.cap[j];
+        rg[j].a = a;
+        rg[j].n = e > a ? e - a : 0;
+        rg[j].na = a & ~3;
+    }
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
+    if (threadIdx.x == 0) tma_mbar_init(bar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t total = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            if (rg[j].n == 0) continue;
+            total += SCH * rg[j].n * 16;
+            if (NRM) total += ((((rg[j].a + rg[j].n + 3) & ~3) - rg[j].na) * 4);
+        }
+        tma_expect(bar, total);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            if (rg[j].n == 0) continue;
+            for (int k = 0; k < SCH; ++k)
+                bulk_g2s(sm + P.spin_off[j] + (size_t)k * P.cap[j] * 16, in_q + ((size_t)k * g.Vh + rg[j].a) * 16,
+                         rg[j].n * 16, bar);
+            if (NRM) {
+                const int ne = (rg[j].a + rg[j].n + 3) & ~3;
+                bulk_g2s(sm + P.nrm_off[j], inn_q + rg[j].na, (ne - rg[j].na) * 4, bar);
+            }
+        }
+    }
+    if (!tma_wait(bar)) {
+        // the copies never completed: report, give them one more bounded wait, write nothing
+        if (A.err) atomicExch(A.err, 1u);
+        tma_wait(bar);
+        return;
+    }
+    const int s = s0 + threadIdx.x;
+    if (s >= g.Vh) return;
+
+    int c[4];
+    cb_coords(g, s, p, c);
+    const int x = c[0], y = c[1], z = c[2], t = c[3];
+    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
+    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
+    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
+    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
+
+    float acc[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+    hop_tma<SP, GP, 0, +1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, xp, y, z, t), xp == 0, acc);
+    hop_tma<SP, GP, 0, -1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, xm, y, z, t), x == 0, acc);
+    hop_tma<SP, GP, 1, +1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, x, yp, z, t), yp == 0, acc);
+    hop_tma<SP, GP, 1, -1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, x, ym, z, t), y == 0, acc);
+    hop_tma<SP, GP, 2, +1>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, cb_index(g, x, y, zp, t), zp == 0, acc);
+    hop_tma<SP, GP, 2, -1>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, cb_index(g, x, y, zm, t), z == 0, acc);
+    hop_tma<SP, GP, 3, +1>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, cb_index(g, x, y, z, tp), tp == 0, acc);
+    hop_tma<SP, GP, 3, -1>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, cb_index(g, x, y, z, tm), t == 0, acc);
+    epilogue<SP, NY>(A, r, p, s, acc);
+}
+
+template <int SP, int GP>
+cudaError_t launch_tma(const DslashArgs& A, int ny, cudaStream_t st)
+{
+    if constexpr (wide_dev<SP>) {
+        return cudaErrorInvalidValue;
+    } else {
+        constexpr bool NRM = SP == P_F16 || SP == P_BF16;
+        const TmaPlan P = tma_plan(A.g.Lxh, nchunk_dev<SP>(), NRM);
+        if (P.bytes > 200 * 1024) return cudaErrorInvalidValue;
+        static bool attr_set[4] = {false, false, false, false};
+        if (!attr_set[ny]) {
+            cudaError_t e = cudaSuccess;
+            const int lim = 200 * 1024;
+            switch (ny) {
+            case 0: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 1: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 2: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 3: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            default: return cudaErrorInvalidValue;
+            }
+            if (e != cudaSuccess) return e;
+            attr_set[ny] = true;
+        }
+        const long long nb = 2LL * ((A.g.Vh + TMA_TB - 1) / TMA_TB) * A.nrhs;
+        if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)nb);
+        switch (ny) {
+        case 0: dslash_tma_kernel<SP, GP, 0><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 1: dslash_tma_kernel<SP, GP, 1><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 2: dslash_tma_kernel<SP, GP, 2><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 3: dslash_tma_kernel<SP, GP, 3><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+}
+
 template <int SP, int GP, int VAR>
 cudaError_t launch_var(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
 {
@@ -478,6 +734,7 @@ cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 bloc
     case 1: return launch_var<SP, GP, 1>(A, ny, grid, block, st);
     case 2: return launch_var<SP, GP, 2>(A, ny, grid, block, st);
     case 3: return launch_staged<SP, GP>(A, ny, grid, block, st);
+    case 4: return launch_tma<SP, GP>(A, ny, st);
     }
     return cudaErrorInvalidValue;
 }

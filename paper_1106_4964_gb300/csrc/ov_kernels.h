@@ -22,10 +22,13 @@ struct DslashArgs {
     double sy[3];
     int nrhs;
     int g5_core, g5_out;
+    unsigned* err;               // set to 1 when a bounded wait of a staged variant times out
 };
-// var: 0 unbounded registers, 1 and 2 capped for occupancy, 3 shared-memory staging (FP32 math, by = 1)
+// var: 0 unbounded registers, 1 and 2 capped for occupancy, 3 per-thread cp.async staging
+// (FP32 math, by = 1), 4 block-wide bulk-copy (TMA) staging of the neighbour ranges (FP32 math;
+// fixed 128-site blocks, bx and by ignored)
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st);
-constexpr int DSLASH_VARIANTS = 4;
+constexpr int DSLASH_VARIANTS = 5;
 
 // ---------------------------------------------------------------- layout conversion
 // canonical complex128 [nrhs][V][12] (device) <-> internal field

@@ -162,3 +162,50 @@ def test_field_dot(prec, tol):
         assert abs(got[r] - ref) <= tol * np.linalg.norm(x[r]) * np.linalg.norm(y[r])
     # bitwise reproducible
     assert np.array_equal(got, ctx.field_dot(fx, fy))
+
+
+# every launch variant the autotuner may pick: (bx, by, variant)
+VARIANTS = [(128, 1, 0), (64, 2, 0), (64, 1, 1), (32, 2, 2), (64, 1, 3), (128, 1, 4)]
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6), (2, 6, 4, 10), (16, 16, 16, 32)])
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_dslash_variants(dims, prec):
+    """Each register-budget and staging variant (including the bulk-copy staged one, whose
+    neighbour ranges are clipped at the array ends and wrap around the lattice) against the
+    oracle, for one and three right-hand sides."""
+    from paper_1106_4964_gb300 import Context
+
+    U = synth.gauge_field(dims, 5, 0.5)
+    psi = synth.gaussian_spinor(dims, 6, nrhs=3)
+    ref = [oracle.dslash(dims, ABC, U, -RHO, psi[r]) for r in range(3)]
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    for bx, by, var in VARIANTS:
+        for nrhs in (1, 3):
+            ctx.set_dslash_shape(prec, nrhs, bx, by, var)
+            src = dev(psi[:nrhs])
+            out = torch.empty_like(src)
+            ctx.apply_dslash(src, out, -RHO, prec=prec)
+            got = host(out)
+            for r in range(nrhs):
+                err = rel(got[r], ref[r])
+                assert err <= TOL[prec], (bx, by, var, nrhs, r, err)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "df64"])
+def test_autotuned_shape_parity(prec):
+    from paper_1106_4964_gb300 import Context
+
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 7, 0.5)
+    psi = synth.gaussian_spinor(dims, 8, nrhs=2)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    for nrhs in (1, 2):
+        shape = ctx.tune_dslash(prec, nrhs)
+        out = torch.empty_like(dev(psi[:nrhs]))
+        ctx.apply_dslash(dev(psi[:nrhs]), out, 0.2, prec=prec)
+        got = host(out)
+        for r in range(nrhs):
+            assert rel(got[r], oracle.dslash(dims, ABC, U, 0.2, psi[r])) <= TOL[prec], shape
