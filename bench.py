@@ -48,6 +48,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_name(prec: str, var: int) -> str:
+    """The CUDA kernel a dslash launch of this precision and launch variant runs."""
+    if var == 3:
+        return f"dslash_staged_kernel<{prec},{prec}>"
+    if var in (4, 5):
+        return f"dslash_tma_kernel<{prec},{prec},links_prefetched={var == 5}>"
+    return f"dslash_kernel<{prec},{prec},variant={var}>"
+
+
 def site_bytes(prec: str, nrhs: int = 1) -> float:
     """Compulsory bytes per site and RHS of a one-pass full D_w: links 48 reals shared by
     the RHS, input and output spinors 24 reals each (16-bit spinors add a 4-byte scale)."""
@@ -251,7 +260,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(bytes_launch),
-                     "kernel": "dslash_kernel<f32,f32,0>"},
+                     "kernel": kernel_name("f32", var)},
         "variants": variants,
         "e2e": e2e,
         "gpu_launches": args.steps * reps,

@@ -153,7 +153,9 @@ int ov_cg_solve(ov_ctx* ctx, const void* b, void* x, int nrhs, double mass, doub
 int ov_net_train(ov_ctx* ctx, int nsolves, int steps, double lr, double mass, double* final_loss, void* stream);
 int ov_net_set_weights(ov_ctx* ctx, const double* w, int n /* 9216 */);
 int ov_net_get_weights(ov_ctx* ctx, double* w, int n /* 9216 */);
-/* out = M in (canonical fields, host or device), computed in FP32. */
+/* out = M in, or (M + M^dag) in / 2 while the option "net_sym" is set (the
+ * default): the operator flexible CG applies.  Canonical fields, host or
+ * device, computed in FP32. */
 int ov_net_apply(ov_ctx* ctx, const void* in, void* out, int nrhs, void* stream);
 /* loss = sum_k |M r_k - e_k|^2 / |e_k|^2 over npairs (<= 16) canonical fields
  * and its gradient (9216 doubles, d/dRe W + i d/dIm W; may be NULL). */
@@ -218,7 +220,9 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *   "reliable_delta" (0.1): ov_cg_solve recomputes the FP64 true residual when
  *                    the inner-precision residual has dropped by this factor;
  *   "filter_hw" (100): Chebyshev filter degree on H_w^2 in ov_deflate(0) (Sec. V: T_100);
- *   "filter_dd" (8):  filter degree on D^dag D in ov_deflate(1);
+ *   "filter_dd" (8):  filter degree on D^dag D in ov_deflate(1) (both rounded down
+ *                    to an even degree and capped so that the filter's dynamic
+ *                    range stays within the work precision);
  *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks the
  *                    "hi_prec" precision when tol < 1e-5 and FP32 otherwise
  *                    (Gram-Schmidt and Rayleigh-Ritz stay FP64), or an ov_prec;

@@ -973,8 +973,8 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
     std::vector<std::tuple<int, int, int>> cand;
     for (int v = 0; v < DSLASH_VARIANTS; ++v) {
         if (v >= 3 && wide(prec)) continue;  // staged variants: FP32 arithmetic only
-        if (v == 4) {                        // bulk-copy staging: fixed 128-site blocks
-            cand.push_back(std::make_tuple(128, 1, 4));
+        if (v >= 4) {                        // bulk-copy staging: fixed 128-site blocks
+            cand.push_back(std::make_tuple(128, 1, v));
             continue;
         }
         const int maxt = v == 0 ? (wide(prec) ? 256 : 512) : (v == 3 ? 128 : 256);

@@ -563,10 +563,11 @@ struct TmaRange {
     int a, n, na;  // first staged index, count, first staged scale index
 };
 
-template <int SP, int GP, int MU, int S>
+// lk: rows 0-1 of the hop's link, loaded before the wait (PRE), else loaded here
+template <int SP, int GP, int MU, int S, bool PRE>
 __device__ __forceinline__ void hop_tma(const DslashArgs& A, const uint8_t* sm, const TmaPlan& P, const TmaRange& rg,
                                         int j, const char* in_q, const float* inn_q, int p, int s, int sn, bool cross,
-                                        float acc[24])
+                                        const float* lk, float acc[24])
 {
     float v[24];
     const int i = sn - rg.a;
@@ -585,18 +586,35 @@ __device__ __forceinline__ void hop_tma(const DslashArgs& A, const uint8_t* sm, 
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] *= ph;
     }
-    const int lpar = S > 0 ? p : 1 - p;
-    const int ls = S > 0 ? s : sn;
-    const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
     float u[18];
-    load_link<GP, float>(lb, A.g.Vh, ls, u);
+    if constexpr (PRE) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) u[k] = lk[k];
+        link_row2<float>(u);
+    } else {
+        const int lpar = S > 0 ? p : 1 - p;
+        const int ls = S > 0 ? s : sn;
+        const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
+        load_link<GP, float>(lb, A.g.Vh, ls, u);
+    }
     float chi[12];
     link_mul<S, float>(u, h, chi);
     accumulate<MU, S, float>(acc, chi);
 }
 
-template <int SP, int GP, int NY>
-__global__ void __launch_bounds__(TMA_TB) dslash_tma_kernel(DslashArgs A)
+template <int GP>
+__device__ __forceinline__ void prefetch_link(const DslashArgs& A, int lpar, int mu, int ls, float w[12])
+{
+    const char* lb = A.gauge + ((size_t)(lpar * 4 + mu) * A.g.Vh) * gauge_link_bytes_dev<GP>();
+    float u[18];
+    load_link_rows<GP, float>(lb, A.g.Vh, ls, u);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w[k] = u[k];
+}
+
+// PRE: every thread loads the rows of its eight links while the bulk copies are in flight
+template <int SP, int GP, int NY, bool PRE>
+__global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashArgs A)
 {
     extern __shared__ __align__(128) uint8_t sm[];
     constexpr int SCH = nchunk_dev<SP>();
@@ -620,6 +638,29 @@ __global__ void __launch_bounds__(TMA_TB) dslash_tma_kernel(DslashArgs A)
         rg[j].n = e > a ? e - a : 0;
         rg[j].na = a & ~3;
     }
+    const int s = s0 + threadIdx.x;
+    int c[4] = {0, 0, 0, 0};
+    if (s < g.Vh) cb_coords(g, s, p, c);
+    const int x = c[0], y = c[1], z = c[2], t = c[3];
+    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
+    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
+    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
+    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
+    const int nb[8] = {cb_index(g, xp, y, z, t), cb_index(g, xm, y, z, t), cb_index(g, x, yp, z, t),
+                       cb_index(g, x, ym, z, t), cb_index(g, x, y, zp, t), cb_index(g, x, y, zm, t),
+                       cb_index(g, x, y, z, tp), cb_index(g, x, y, z, tm)};
+    float lk[PRE ? 8 : 1][12];
+    if constexpr (PRE) {
+        if (s < g.Vh) {
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int mu = h >> 1;
+                const bool fwd = (h & 1) == 0;
+                prefetch_link<GP>(A, fwd ? p : q, mu, fwd ? s : nb[h], lk[h]);
+            }
+        }
+    }
+
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
     if (threadIdx.x == 0) tma_mbar_init(bar);
     __syncthreads();
@@ -650,32 +691,23 @@ __global__ void __launch_bounds__(TMA_TB) dslash_tma_kernel(DslashArgs A)
         tma_wait(bar);
         return;
     }
-    const int s = s0 + threadIdx.x;
     if (s >= g.Vh) return;
-
-    int c[4];
-    cb_coords(g, s, p, c);
-    const int x = c[0], y = c[1], z = c[2], t = c[3];
-    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
-    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
-    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
-    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
 
     float acc[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_tma<SP, GP, 0, +1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, xp, y, z, t), xp == 0, acc);
-    hop_tma<SP, GP, 0, -1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, xm, y, z, t), x == 0, acc);
-    hop_tma<SP, GP, 1, +1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, x, yp, z, t), yp == 0, acc);
-    hop_tma<SP, GP, 1, -1>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, cb_index(g, x, ym, z, t), y == 0, acc);
-    hop_tma<SP, GP, 2, +1>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, cb_index(g, x, y, zp, t), zp == 0, acc);
-    hop_tma<SP, GP, 2, -1>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, cb_index(g, x, y, zm, t), z == 0, acc);
-    hop_tma<SP, GP, 3, +1>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, cb_index(g, x, y, z, tp), tp == 0, acc);
-    hop_tma<SP, GP, 3, -1>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, cb_index(g, x, y, z, tm), t == 0, acc);
+    hop_tma<SP, GP, 0, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[0], xp == 0, lk[0], acc);
+    hop_tma<SP, GP, 0, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[1], x == 0, lk[PRE ? 1 : 0], acc);
+    hop_tma<SP, GP, 1, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[2], yp == 0, lk[PRE ? 2 : 0], acc);
+    hop_tma<SP, GP, 1, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[3], y == 0, lk[PRE ? 3 : 0], acc);
+    hop_tma<SP, GP, 2, +1, PRE>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, nb[4], zp == 0, lk[PRE ? 4 : 0], acc);
+    hop_tma<SP, GP, 2, -1, PRE>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, nb[5], z == 0, lk[PRE ? 5 : 0], acc);
+    hop_tma<SP, GP, 3, +1, PRE>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, nb[6], tp == 0, lk[PRE ? 6 : 0], acc);
+    hop_tma<SP, GP, 3, -1, PRE>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, nb[7], t == 0, lk[PRE ? 7 : 0], acc);
     epilogue<SP, NY>(A, r, p, s, acc);
 }
 
-template <int SP, int GP>
+template <int SP, int GP, bool PRE>
 cudaError_t launch_tma(const DslashArgs& A, int ny, cudaStream_t st)
 {
     if constexpr (wide_dev<SP>) {
@@ -689,10 +721,10 @@ cudaError_t launch_tma(const DslashArgs& A, int ny, cudaStream_t st)
             cudaError_t e = cudaSuccess;
             const int lim = 200 * 1024;
             switch (ny) {
-            case 0: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 1: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 2: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 3: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 0: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 0, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 1: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 1, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 2: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 2, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
+            case 3: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 3, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
             default: return cudaErrorInvalidValue;
             }
             if (e != cudaSuccess) return e;
@@ -702,10 +734,10 @@ cudaError_t launch_tma(const DslashArgs& A, int ny, cudaStream_t st)
         if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
         const dim3 grid((unsigned)nb);
         switch (ny) {
-        case 0: dslash_tma_kernel<SP, GP, 0><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 1: dslash_tma_kernel<SP, GP, 1><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 2: dslash_tma_kernel<SP, GP, 2><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 3: dslash_tma_kernel<SP, GP, 3><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 0: dslash_tma_kernel<SP, GP, 0, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 1: dslash_tma_kernel<SP, GP, 1, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 2: dslash_tma_kernel<SP, GP, 2, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
+        case 3: dslash_tma_kernel<SP, GP, 3, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
@@ -734,7 +766,8 @@ cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 bloc
     case 1: return launch_var<SP, GP, 1>(A, ny, grid, block, st);
     case 2: return launch_var<SP, GP, 2>(A, ny, grid, block, st);
     case 3: return launch_staged<SP, GP>(A, ny, grid, block, st);
-    case 4: return launch_tma<SP, GP>(A, ny, st);
+    case 4: return launch_tma<SP, GP, false>(A, ny, st);
+    case 5: return launch_tma<SP, GP, true>(A, ny, st);
     }
     return cudaErrorInvalidValue;
 }

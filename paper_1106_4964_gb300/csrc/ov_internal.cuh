@@ -289,7 +289,7 @@ __device__ __forceinline__ void store_spinor(char* __restrict__ base, float* __r
 // `base` points at link[p][mu] chunk 0.
 // ---------------------------------------------------------------------------
 template <int P, typename Real>
-__device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh, int s, Real u[18])
+__device__ __forceinline__ void load_link_rows(const char* __restrict__ base, int Vh, int s, Real u[18])
 {
     if constexpr (P == P_DF64) {
         const float4* b = reinterpret_cast<const float4*>(base);
@@ -329,7 +329,12 @@ __device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh,
             u[4 * k + 3] = a1.y;
         }
     }
-    // row 2 = conj(row0 x row1)  (unitarity and det = 1)
+}
+
+// row 2 = conj(row0 x row1)  (unitarity and det = 1)
+template <typename Real>
+__device__ __forceinline__ void link_row2(Real u[18])
+{
     // (r0 x r1)_0 = r0_1 r1_2 - r0_2 r1_1, _1 = r0_2 r1_0 - r0_0 r1_2, _2 = r0_0 r1_1 - r0_1 r1_0
 #define OV_RE(i) u[2 * (i)]
 #define OV_IM(i) u[2 * (i) + 1]
@@ -344,6 +349,13 @@ __device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh,
     }
 #undef OV_RE
 #undef OV_IM
+}
+
+template <int P, typename Real>
+__device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh, int s, Real u[18])
+{
+    load_link_rows<P, Real>(base, Vh, s, u);
+    link_row2<Real>(u);
 }
 
 }  // namespace ov

@@ -375,7 +375,9 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         const double y0 = (bmax + acut) / (bmax - acut);
         const double limit = W.tmp[0].prec == P_F64 ? 1e12 : (W.tmp[0].prec == P_DF64 ? 1e10 : 1e4);
         const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
-        Keff = std::max(2, std::min(K, kmax));
+        // even degree: T_K is then positive below the cutoff, so the wanted eigenvalues are the
+        // largest of the filter (an odd degree would send them to large negative values)
+        Keff = std::max(2, std::min(K, kmax)) & ~1;
     }
     OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
         OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, in, o, W.tmp, st));

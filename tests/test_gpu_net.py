@@ -29,13 +29,17 @@ def rand_weights(seed):
     return w1, w2
 
 
-def test_net_forward_parity():
+@pytest.mark.parametrize("sym", [0, 1])
+def test_net_forward_parity(sym):
+    """M x (sym = 0) and the symmetrised (M + M^dag) x / 2 that flexible CG applies (sym = 1);
+    the oracle's M^dag is the input gradient of its layers, L1^dag L2^dag."""
     from paper_1106_4964_gb300 import Context
 
     dims = (4, 4, 4, 6)
     U = synth.gauge_field(dims, 21, 0.6)
     ctx = Context(dims, ABC)
     ctx.set_gauge(dev(U))
+    ctx.set_option("net_sym", sym)
     w1, w2 = rand_weights(0)
     ctx.net_set_weights(np.concatenate([w1.reshape(-1), w2.reshape(-1)]))
     x = synth.gaussian_spinor(dims, 3, nrhs=2)
@@ -44,6 +48,11 @@ def test_net_forward_parity():
     got = host(out)
     for r in range(2):
         ref = oracle.net_apply(dims, ABC, U, w1, w2, x[r]).reshape(x[r].shape)
+        if sym:
+            h = oracle.net_layer(dims, ABC, U, w1, x[r])
+            g2, _ = oracle.net_layer_grad(dims, ABC, U, w2, h, x[r])
+            g1, _ = oracle.net_layer_grad(dims, ABC, U, w1, x[r], g2)
+            ref = 0.5 * (ref + g1[0].reshape(x[r].shape))
         assert rel(got[r], ref) <= FWD_TOL
 
 
