@@ -59,6 +59,15 @@ def lib():
     return _lib
 
 
+def threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().or_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(ctypes.c_int(int(n)))
+
+
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 

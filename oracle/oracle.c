@@ -23,10 +23,15 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
 typedef double complex cplx;
+
+/* OpenMP threads the parallel loops use, and a way to set them (CPU timing) */
+int or_threads(void) { return omp_get_max_threads(); }
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
 
 /* ------------------------------------------------------------------ */
 /* gamma matrices                                                       */
