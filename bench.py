@@ -515,15 +515,29 @@ def run_propagator(args):
     b = torch.from_numpy(synth.point_sources(dims)).cuda()
     for p in ("f32", "f16", args.hi_prec):
         ctx.tune_dslash(p, 12)
-    out = {}
-    for inner in args.cg_inner.split(","):
-        x = torch.empty_like(b)
-        info = ctx.cg_solve(b, x, mass=args.mass, tol=1e-10, max_iter=args.max_iter, inner_prec=inner)
-        out[inner] = {"seconds": round(info["seconds"], 2), "iterations": info["iterations"],
-                      "reliable_updates": info["reliable_updates"],
-                      "max_true_residual": max(info["true_residual"]),
-                      "solves_per_s": round(12 / info["seconds"], 4)}
-    best = min(out.values(), key=lambda d: d["seconds"])
+    def solve(src, inner):
+        x = torch.empty_like(src)
+        n0 = ctx.dslash_count()
+        info = ctx.cg_solve(src, x, mass=args.mass, tol=1e-10, max_iter=args.max_iter, inner_prec=inner)
+        nrhs = src.shape[0]
+        return {"seconds": round(info["seconds"], 2), "iterations": info["iterations"],
+                "reliable_updates": info["reliable_updates"], "dslash_launches": ctx.dslash_count() - n0,
+                "max_true_residual": max(info["true_residual"][:nrhs]),
+                "solves_per_s": round(nrhs / info["seconds"], 4)}
+
+    out = {inner: solve(b, inner) for inner in args.cg_inner.split(",")}
+    best_inner = min(out, key=lambda k: out[k]["seconds"])
+    best = out[best_inner]
+    # the same method one source at a time (no batching), and the plain FP64 method
+    compare = {}
+    if args.plain_rhs > 0:
+        compare[f"unbatched_{best_inner}"] = solve(b[:1], best_inner)
+        ctx.set_option("chiral", 0)
+        ctx.set_option("hi_prec", ov.PREC["f64"])
+        ctx.tune_dslash("f64", args.plain_rhs)
+        compare["plain_f64"] = solve(b[:args.plain_rhs], "f64")
+        compare["plain_f64"]["note"] = (f"FP64 inner operator and true residuals, full D^dag D, "
+                                        f"{args.plain_rhs} of the 12 sources")
     print(json.dumps({
         "metric": "overlap propagator solves/s at res 1e-10", "value": best["solves_per_s"], "unit": "solves/s",
         "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(1e3 * best["seconds"], 1),
@@ -535,7 +549,7 @@ def run_propagator(args):
                    "lattice": list(dims), "eps": eps, "lambda_max": lmax, "hi_prec": args.hi_prec,
                    "chiral": bool(args.chiral)},
         "propagators_per_s": round(best["solves_per_s"] / 12, 5),
-        "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out}))
+        "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out, "compare": compare}))
 
 
 def run_learned(args):
@@ -556,6 +570,8 @@ def run_learned(args):
         U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
         ctx = ov.Context(dims, BC)
         ctx.set_gauge(torch.from_numpy(U).cuda())
+        ctx.set_option("hi_prec", ov.PREC[args.hi_prec])
+        ctx.set_option("chiral", int(args.chiral))
         ctx.set_sign_poly(RHO, 0.05, args.degree, 0.0)
         lmax = ctx.get_sign_poly()["lambda_max"]
         eps = 0.05
@@ -589,7 +605,8 @@ def run_learned(args):
         "metric": "time to 1e-10, learned flexible CG vs plain deflated CG", "value": res["learned"]["seconds"],
         "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * res["learned"]["seconds"],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f64", "data": "synthetic",
-        "config": {"workload": f"train {small}, apply {big}, 12 point sources, mass {args.mass}"}, "results": res}))
+        "config": {"workload": f"train {small}, apply {big}, 12 point sources, mass {args.mass}",
+                   "hi_prec": args.hi_prec, "chiral": bool(args.chiral)}, "results": res}))
 
 
 def main():
@@ -615,6 +632,8 @@ def main():
     ap.add_argument("--mass", type=float, default=0.0)
     ap.add_argument("--delta", type=float, default=0.1)
     ap.add_argument("--cg-inner", default="f32", help="inner precisions of the propagator CG, comma separated")
+    ap.add_argument("--plain-rhs", type=int, default=1,
+                    help="propagator: also solve this many sources with the plain FP64 method (0: skip)")
     ap.add_argument("--chiral", type=int, default=0, choices=[0, 1],
                     help="propagator CG and D^dag D deflation on chiral sectors (one sign per application)")
     ap.add_argument("--hi-prec", default="f64", choices=["f64", "df64"],

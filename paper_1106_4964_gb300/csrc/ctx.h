@@ -26,7 +26,7 @@ namespace ov {
 constexpr int DSCAL_DOUBLES = 65536;
 constexpr int DSCAL_COEF = 57344;   // [0, DSCAL_COEF): coefficient blocks (double2 pairs)
 constexpr int DSCAL_CGCO = 57344;   // double2 [K][R] per-rhs coefficients
-constexpr int DSCAL_CHCO = 59392;   // double2 [3][R] coefficients of the chiral-sector operator
+constexpr int DSCAL_CHCO = 59392;   // double2 [3][R] chiral-sector operator, [2][R] sector projection
 constexpr int DSCAL_NORM = 61440;   // per-rhs norms
 constexpr int DSCAL_DOT = 62464;    // per-rhs dots (double2)
 constexpr int DSCAL_TMP = 64512;    // single-value scratch

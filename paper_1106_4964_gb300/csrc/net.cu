@@ -560,6 +560,12 @@ int ov_net_train(ov_ctx* c, int nsolves, int steps, double lr, double mass, doub
     n->trained = 0;
     for (int s = 0; s < nsolves && n->npairs < n->cap; ++s) {
         OV_CUDA(c, launch_fill_random(c->g, b, 9001ull + s, st));
+        if (c->chiral) {  // chiral-sector solves need sources of definite chirality: alternate the sectors
+            const double chi = (s & 1) ? -1.0 : 1.0;
+            FieldDesc v2[2] = {b, b};
+            double2 h2[2] = {make_double2(0.5, 0), make_double2(0.5 * chi, 0)};
+            OV_TRY(lincomb(c, b, 2, v2, h2, nullptr, 2, nullptr, st));
+        }
         const int first = n->npairs;
         n->recording = 1;
         FieldDesc bb, xx;

@@ -734,7 +734,8 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
         std::vector<double2> hg(R);
         OV_TRY(to_host(c, ddt, hg.data(), R * sizeof(double2), st));
         const double cm = (c->rho * c->rho - 0.25 * mass * mass) / c->rho;
-        std::vector<double2> hc(3 * R);
+        // [3][R] operator coefficients, then [2][R] sector projection (1/2, chi/2)
+        std::vector<double2> hc(5 * R);
         for (int q = 0; q < R; ++q) {
             const double n2 = bn[q] * bn[q];
             if (!(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
@@ -743,11 +744,21 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
             hc[q] = make_double2(mass * mass, 0);
             hc[R + q] = make_double2(cm, 0);
             hc[2 * R + q] = make_double2(chi * cm, 0);
+            hc[3 * R + q] = make_double2(0.5, 0);
+            hc[4 * R + q] = make_double2(0.5 * chi, 0);
         }
         OV_TRY(to_dev(c, hc.data(), (void*)dch, hc.size() * sizeof(double2), st));
     }
     auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
         return c->chiral ? chiral_apply(c, in, out, mass, dch, st) : normal_apply(c, in, out, mass, st);
+    };
+    // z = M r; in chiral mode projected back onto each right-hand side's sector, z <- (1 + chi gamma5) z / 2
+    // (the network mixes chiralities), so that the search directions stay where the operator acts
+    auto precond_apply = [&]() -> int {
+        OV_TRY(net_apply_precond(c, rs, zs, st));
+        if (!c->chiral) return OV_OK;
+        FieldDesc v2[2] = {zs, zs};
+        return lincomb(c, zs, 2, v2, nullptr, dch + 3 * R, 2, nullptr, st);
     };
 
     std::vector<double> rr(R), rr_new(R), rmax(R), res(R, 1.0), rz(R);
@@ -806,7 +817,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // start (or restart) the search direction: p = z = M r (preconditioned) or p = r
     auto start_direction = [&]() -> int {
         if (use_prec) {
-            OV_TRY(net_apply_precond(c, rs, zs, st));
+            OV_TRY(precond_apply());
             OV_TRY(project(xis, zs));
             OV_TRY(copy_field(c, zs, ps, st));
             OV_TRY(dot(c, rs, zs, ddt, st));
@@ -902,7 +913,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
             // next direction
             std::vector<double> rz_new(R);
             if (use_prec) {
-                OV_TRY(net_apply_precond(c, rs, zs, st));
+                OV_TRY(precond_apply());
                 OV_TRY(project(xis, zs));
                 // flexible CG (Polak-Ribiere form): beta = z_new^dag (r_new - r_old) / (z_old^dag r_old)
                 FieldDesc v[2] = {rs, rold};
