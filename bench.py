@@ -313,6 +313,30 @@ def cpu_baseline(U, psi, args):
                       "algorithmic-bytes unit as the GPU line"}
 
 
+def cpu_dw_extrapolation(U, dims, launches, args):
+    """Oracle estimate of one solve: the FP64 oracle's D_w timed on this lattice (whole
+    applications for about --cpu-seconds), times the D_w applications per source of the GPU
+    solve (each multi-RHS launch applies D_w once per right-hand side).  Vector updates and
+    projections are left out, so the estimate favours the CPU."""
+    import oracle
+    import synth
+
+    oracle.build()
+    psi = synth.gaussian_spinor(dims, seed=2, nrhs=1)[0]
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.dslash(dims, BC, U, -RHO, psi)
+        n += 1
+        if time.perf_counter() - t0 > min(args.cpu_seconds, 10.0):
+            break
+    dt = (time.perf_counter() - t0) / n
+    t_solve = dt * launches
+    return {"value": round(1.0 / t_solve, 6), "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n} FP64 oracle D_w applications on {dims[0]}^3x{dims[3]} ({dt * 1e3:.1f} ms each), "
+                      f"extrapolated to the {launches} D_w applications per source of the GPU solve"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -413,6 +437,11 @@ def run_overlap(args):
             fi.close()
             fo.close()
     main = res["f32_r1"]
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_dw_extrapolation(U, dims, 2 * args.degree + 1, args)
+        cpu["value"], cpu["unit"] = cpu["value"], "applications/s"
+        cpu["sample"] = cpu["sample"].replace("per source of the GPU solve", "of one overlap application")
     print(json.dumps({
         "metric": "overlap applications/s", "value": main["applications_per_s"], "unit": "applications/s",
         "n_gpus": 1, "steps": args.reps, "warmup": 1, "ms_per_step": main["ms"], "higher_is_better": True,
@@ -422,7 +451,7 @@ def run_overlap(args):
                    "lambda_max": lmax},
         "setup_s": {"lambda_max": round(t_lmax, 2), "deflate": round(t_defl, 2)},
         "eigen": {"nev": int(len(vals)), "min_abs": float(np.abs(vals).min()), "max_abs": float(np.abs(vals).max())},
-        "precisions": res}))
+        "precisions": res, "cpu_baseline": cpu}))
 
 
 def run_project(args):
@@ -538,6 +567,9 @@ def run_propagator(args):
         compare["plain_f64"] = solve(b[:args.plain_rhs], "f64")
         compare["plain_f64"]["note"] = (f"FP64 inner operator and true residuals, full D^dag D, "
                                         f"{args.plain_rhs} of the 12 sources")
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_dw_extrapolation(U, dims, best["dslash_launches"], args)
     print(json.dumps({
         "metric": "overlap propagator solves/s at res 1e-10", "value": best["solves_per_s"], "unit": "solves/s",
         "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": round(1e3 * best["seconds"], 1),
@@ -549,7 +581,8 @@ def run_propagator(args):
                    "lattice": list(dims), "eps": eps, "lambda_max": lmax, "hi_prec": args.hi_prec,
                    "chiral": bool(args.chiral)},
         "propagators_per_s": round(best["solves_per_s"] / 12, 5),
-        "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out, "compare": compare}))
+        "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out, "compare": compare,
+        "cpu_baseline": cpu}))
 
 
 def run_learned(args):

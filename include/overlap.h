@@ -96,6 +96,14 @@ int ov_apply_dslash(ov_ctx* ctx, const void* in, void* out, double m, int nrhs, 
 /* out = H_w in = gamma5 D_w(m) in (Sec. II; hermitian by gamma5-hermiticity). */
 int ov_apply_Hw(ov_ctx* ctx, const void* in, void* out, double m, int nrhs, int prec, void* stream);
 
+/* out = D(m)^dag D(m) in, the operator of ov_cg_solve (Eqs. 3, 8; the
+ * sign polynomial and H_w eigenpairs as for ov_apply_overlap).  chiral = 1:
+ * the one-sign chiral-sector form m^2 + (rho^2 - m^2/4)/rho (1 + chi gamma5)
+ * D(0), equal to it up to the polynomial's error on fields with
+ * gamma5 in = chi in; every right-hand side must have definite chirality
+ * (else OV_EINVAL).  Canonical fields, host or device. */
+int ov_apply_normal(ov_ctx* ctx, const void* in, void* out, double mass, int nrhs, int prec, int chiral,
+                    void* stream);
 /* Fix the sign-function polynomial (Eqs. 4-5, Sec. V): rho (the overlap
  * parameter, H_w = gamma5 D_w(-rho)), P = the degree-`degree` Chebyshev
  * interpolant of x^{-1/2} on [eps, 1], evaluated on Q^2 with

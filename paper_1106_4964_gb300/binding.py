@@ -54,6 +54,7 @@ _SIGS = {
     "ov_set_sign_poly": (_I, [_P, _D, _D, _I, _D]),
     "ov_get_sign_poly": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "ov_apply_overlap": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "ov_apply_normal": (_I, [_P, _P, _P, _D, _I, _I, _I, _P]),
     "ov_deflate": (_I, [_P, _I, _I, _D, _P]),
     "ov_set_eigenpairs": (_I, [_P, _I, _I, _P, _P, _P]),
     "ov_get_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P]),
@@ -237,6 +238,11 @@ class Context:
     def apply_overlap(self, x, out, mass=0.0, prec="f64", stream=None):
         self._check(self.lib.ov_apply_overlap(self.h, _ptr(x), _ptr(out), float(mass), self._nrhs(x), _prec(prec),
                                               _stream(stream)))
+        return out
+
+    def apply_normal(self, x, out, mass=0.0, prec="f64", chiral=0, stream=None):
+        self._check(self.lib.ov_apply_normal(self.h, _ptr(x), _ptr(out), float(mass), self._nrhs(x), _prec(prec),
+                                             int(chiral), _stream(stream)))
         return out
 
     def deflate(self, which, nev, tol, stream=None):

@@ -2,6 +2,7 @@
 // application, internal-layout fields.  The solvers (Lanczos, CG) live in
 // solver.cu, the learned preconditioner in net.cu.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "ctx.h"
@@ -160,6 +161,15 @@ int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cuda
 }
 
 int gauge_prec_for(int prec) { return prec; }
+
+bool verbose()
+{
+    static const bool v = [] {
+        const char* e = std::getenv("OV_VERBOSE");
+        return e && e[0] == '1';
+    }();
+    return v;
+}
 
 // Flags set by kernels whose bounded waits ran out (derr[2]); read and cleared.
 int check_kernel_flags(ov_ctx* c, cudaStream_t st)
@@ -477,6 +487,42 @@ int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double ma
     });
 }
 
+// Chirality chi_r of every right-hand side of f (f^dag gamma5 f = chi |f|^2 to 1e-12, else
+// OV_EINVAL) and the chiral-sector coefficients at DSCAL_CHCO: [3][R] for chiral_apply, then
+// [2][R] = (1/2, chi/2) for the sector projection.  tmp: a field of f's shape (overwritten).
+int chiral_setup(ov_ctx* c, const FieldDesc& f, const FieldDesc& tmp, double mass, cudaStream_t st)
+{
+    const int R = f.nrhs;
+    if (5 * R * 2 > DSCAL_NORM - DSCAL_CHCO) return set_err(c, OV_EINVAL, "chiral: too many right-hand sides");
+    double2* ddt = (double2*)(c->dscal + DSCAL_DOT);
+    std::vector<double2> hn(R), hg(R);
+    OV_TRY(norm2(c, f, (double*)ddt, st));
+    OV_CUDA(c, cudaMemcpyAsync(hn.data(), ddt, R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    FieldDesc v1[1] = {f};
+    const double2 one[1] = {make_double2(1, 0)};
+    OV_TRY(lincomb(c, tmp, 1, v1, one, nullptr, 1, nullptr, st));  // tmp = gamma5 f
+    OV_TRY(dot(c, f, tmp, ddt, st));
+    OV_CUDA(c, cudaMemcpyAsync(hg.data(), ddt, R * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    const double cm = (c->rho * c->rho - 0.25 * mass * mass) / c->rho;
+    std::vector<double2> hc(5 * R);
+    for (int q = 0; q < R; ++q) {
+        const double n2 = hn[q].x;
+        if (!(n2 > 0) || !(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
+            return set_err(c, OV_EINVAL, "chiral mode needs right-hand sides of definite chirality (rhs %d)", q);
+        const double chi = hg[q].x > 0 ? 1.0 : -1.0;
+        hc[q] = make_double2(mass * mass, 0);
+        hc[R + q] = make_double2(cm, 0);
+        hc[2 * R + q] = make_double2(chi * cm, 0);
+        hc[3 * R + q] = make_double2(0.5, 0);
+        hc[4 * R + q] = make_double2(0.5 * chi, 0);
+    }
+    OV_CUDA(c, cudaMemcpyAsync(c->dscal + DSCAL_CHCO, hc.data(), hc.size() * sizeof(double2),
+                               cudaMemcpyHostToDevice, st));
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    return OV_OK;
+}
+
 // Chebyshev-interpolant coefficients of x^{-1/2} on [eps, 1] at the n+1
 // Chebyshev nodes of the variable y = (2x - (1+eps))/(1-eps) (Eq. 4, Sec. V);
 // c_0 is halved so that P = sum_k c_k T_k(y).
@@ -625,10 +671,16 @@ static int apply_canonical(ov_ctx* c, const void* in, void* out, double m, int n
     OV_TRY(ws_field(c, WS_IN, prec, nrhs, &fi));
     OV_TRY(ws_field(c, WS_OUT, prec, nrhs, &fo));
     OV_CUDA(c, launch_pack(c->g, din, fi, 0, st));
-    if (kind == 2)
+    if (kind == 2) {
         OV_TRY(overlap_apply(c, fi, fo, m, st));
-    else
+    } else if (kind == 3) {
+        OV_TRY(normal_apply(c, fi, fo, m, st));
+    } else if (kind == 4) {
+        OV_TRY(chiral_setup(c, fi, fo, m, st));
+        OV_TRY(chiral_apply(c, fi, fo, m, (const double2*)(c->dscal + DSCAL_CHCO), st));
+    } else {
         OV_TRY(dslash_apply(c, fi, fo, 4.0 + m, -0.5, kind == 1, 0, 0, nullptr, nullptr, st));
+    }
     OV_CUDA(c, launch_unpack(c->g, fo, dout, 0, st));
     OV_TRY(stage_out_finish(c, out, dout, bytes, st));
     return check_kernel_flags(c, st);
@@ -649,6 +701,14 @@ int ov_apply_overlap(ov_ctx* c, const void* in, void* out, double mass, int nrhs
     if (!c) return OV_EINVAL;
     if (!c->have_poly) return set_err(c, OV_ESTATE, "overlap: no sign polynomial (call ov_set_sign_poly)");
     return apply_canonical(c, in, out, mass, nrhs, prec, stream, 2);
+}
+
+int ov_apply_normal(ov_ctx* c, const void* in, void* out, double mass, int nrhs, int prec, int chiral,
+                    void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (!c->have_poly) return set_err(c, OV_ESTATE, "normal: no sign polynomial (call ov_set_sign_poly)");
+    return apply_canonical(c, in, out, mass, nrhs, prec, stream, chiral ? 4 : 3);
 }
 
 int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambda_max)
@@ -1001,6 +1061,9 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
         OV_CUDA(c, cudaEventSynchronize(e1));
         float ms = 0;
         OV_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (verbose())
+            fprintf(stderr, "[ov] tune prec %d nrhs %d: block %d x %d variant %d: %.2f us\n", prec, nrhs,
+                    std::get<0>(sh), std::get<1>(sh), std::get<2>(sh), 100.0f * ms);
         if (ms < best) {
             best = ms;
             bsh = sh;

@@ -137,6 +137,8 @@ int stage_out_buffer(ov_ctx* c, int which, void* dst, size_t bytes, double** dev
 int stage_out_finish(ov_ctx* c, void* dst, const double* dev, size_t bytes, cudaStream_t st);
 int gauge_prec_for(int prec);
 int check_kernel_flags(ov_ctx* c, cudaStream_t st);
+// progress lines of the iterative solvers on stderr when the environment sets OV_VERBOSE=1
+bool verbose();
 int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out);
 
 // operators on internal fields
@@ -147,6 +149,7 @@ int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double m
 int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
 int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, const double2* dcoef,
                  cudaStream_t st);
+int chiral_setup(ov_ctx* c, const FieldDesc& f, const FieldDesc& tmp, double mass, cudaStream_t st);
 
 // level-1 helpers (stream-ordered); results of reductions land in device memory
 int lincomb(ov_ctx* c, const FieldDesc& out, int K, const FieldDesc* x, const double2* hcoef, const double2* dcoef,

@@ -471,7 +471,7 @@ cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cu
 // right-hand sides of one site block read the same links back to back (L2).
 // ---------------------------------------------------------------------------
 constexpr int TMA_TB = 128;                 // sites per block
-constexpr long long TMA_SPIN = 1ll << 22;   // bounded mbarrier wait
+constexpr long long TMA_SPIN = 1ll << 22;   // bounded mbarrier wait (polls; also 2 s of wall time)
 
 struct TmaPlan {
     int cap[5];        // slots per range
@@ -508,7 +508,9 @@ __device__ __forceinline__ void tma_expect(uint64_t* b, uint32_t bytes)
 }
 __device__ __forceinline__ bool tma_wait(uint64_t* b)
 {
+    const unsigned long long t0 = global_ns();
     for (long long i = 0; i < TMA_SPIN; ++i) {
+        if ((i & 1023) == 1023 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"

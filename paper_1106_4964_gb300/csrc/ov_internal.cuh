@@ -105,6 +105,15 @@ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b;
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
+// Nanoseconds of the GPU's global timer (bounds the wall time of every spin-wait).
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+
 struct Geom {
     int L[4];   // Lx, Ly, Lz, Lt
     int Lxh;    // Lx / 2

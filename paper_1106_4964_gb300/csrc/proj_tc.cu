@@ -60,8 +60,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
 // bounded wait; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
 {
-    for (long long i = 0; i < TC_SPIN; ++i)
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0; i < TC_SPIN; ++i) {
         if (mbar_try(b, parity)) return true;
+        if ((i & 1023) == 1023 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
     return false;
 }
 

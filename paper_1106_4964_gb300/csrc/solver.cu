@@ -379,6 +379,9 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         // largest of the filter (an odd degree would send them to large negative values)
         Keff = std::max(2, std::min(K, kmax)) & ~1;
     }
+    if (verbose())
+        fprintf(stderr, "[ov] lanczos chi=%d nev=%d m=%d: cut %.4e of %.4e, filter degree %d (asked %d)\n", chi, nev,
+                m, acut, bmax, Keff, K);
     OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
         OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, in, o, W.tmp, st));
         return project_chiral(c, o, chi, st);
@@ -468,6 +471,9 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 OV_TRY(status);
                 maxres = std::max(maxres, r / rscale);
             }
+            if (verbose())
+                fprintf(stderr, "[ov] lanczos restart %d: %d/%d filter pairs converged, max eigen-residual %.3e\n",
+                        restart, nconv, nev, maxres);
             if (maxres <= tol) {
                 OV_CUDA(c, cudaMemcpyAsync(out.data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
                 OV_CUDA(c, cudaStreamSynchronize(st));
@@ -726,29 +732,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // chiral-sector inner operator: every right-hand side must have definite chirality
     // (b^dag gamma5 b = +-|b|^2); the true residuals keep the full D^dag D
     const double2* dch = (const double2*)(c->dscal + DSCAL_CHCO);
-    if (c->chiral) {
-        FieldDesc v1[1] = {b};
-        double2 one[1] = {make_double2(1, 0)};
-        OV_TRY(lincomb(c, t, 1, v1, one, nullptr, 1, nullptr, st));  // t = gamma5 b
-        OV_TRY(dot(c, b, t, ddt, st));
-        std::vector<double2> hg(R);
-        OV_TRY(to_host(c, ddt, hg.data(), R * sizeof(double2), st));
-        const double cm = (c->rho * c->rho - 0.25 * mass * mass) / c->rho;
-        // [3][R] operator coefficients, then [2][R] sector projection (1/2, chi/2)
-        std::vector<double2> hc(5 * R);
-        for (int q = 0; q < R; ++q) {
-            const double n2 = bn[q] * bn[q];
-            if (!(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
-                return set_err(c, OV_EINVAL, "cg: chiral mode needs right-hand sides of definite chirality (rhs %d)", q);
-            const double chi = hg[q].x > 0 ? 1.0 : -1.0;
-            hc[q] = make_double2(mass * mass, 0);
-            hc[R + q] = make_double2(cm, 0);
-            hc[2 * R + q] = make_double2(chi * cm, 0);
-            hc[3 * R + q] = make_double2(0.5, 0);
-            hc[4 * R + q] = make_double2(0.5 * chi, 0);
-        }
-        OV_TRY(to_dev(c, hc.data(), (void*)dch, hc.size() * sizeof(double2), st));
-    }
+    if (c->chiral) OV_TRY(chiral_setup(c, b, t, mass, st));
     auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
         return c->chiral ? chiral_apply(c, in, out, mass, dch, st) : normal_apply(c, in, out, mass, st);
     };
@@ -889,6 +873,11 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
                 OV_CUDA(c, cudaMemsetAsync(xs.data, 0, xs.rhs_bytes() * R, st));
                 if (xs.norm) OV_CUDA(c, cudaMemsetAsync(xs.norm, 0, (size_t)2 * xs.Vh * 4 * R, st));
                 OV_TRY(refresh(all_done));
+                if (verbose()) {
+                    double w = 0;
+                    for (int q = 0; q < R; ++q) w = std::max(w, res[q]);
+                    fprintf(stderr, "[ov] cg iteration %d: true residual %.3e (update %d)\n", iters, w, updates);
+                }
                 if (all_done) break;
                 double worst = 0;
                 for (int q = 0; q < R; ++q)
