@@ -573,6 +573,9 @@ int ov_create(ov_ctx** ctx, const int dims[4], const double bc_phase[4])
     }
     c->g.Lxh = dims[0] / 2;
     c->g.Vh = (int)(V / 2);
+    c->g.fxh = FastDiv((uint32_t)c->g.Lxh);
+    c->g.fy = FastDiv((uint32_t)dims[1]);
+    c->g.fz = FastDiv((uint32_t)dims[2]);
     cudaGetDevice(&c->device);
     void* p = nullptr;
     if (dev_alloc(c, &p, DSCAL_DOUBLES * sizeof(double)) != OV_OK) {

@@ -181,24 +181,19 @@ __global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) 
 
     int c[4];
     cb_coords(g, s, p, c);
-    const int x = c[0], y = c[1], z = c[2], t = c[3];
-    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
-    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
-    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
-    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
-
     Real acc[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = 0;
 
-    hop<SP, GP, 0, +1>(A, in_q, inn_q, p, s, cb_index(g, xp, y, z, t), xp == 0, acc);
-    hop<SP, GP, 0, -1>(A, in_q, inn_q, p, s, cb_index(g, xm, y, z, t), x == 0, acc);
-    hop<SP, GP, 1, +1>(A, in_q, inn_q, p, s, cb_index(g, x, yp, z, t), yp == 0, acc);
-    hop<SP, GP, 1, -1>(A, in_q, inn_q, p, s, cb_index(g, x, ym, z, t), y == 0, acc);
-    hop<SP, GP, 2, +1>(A, in_q, inn_q, p, s, cb_index(g, x, y, zp, t), zp == 0, acc);
-    hop<SP, GP, 2, -1>(A, in_q, inn_q, p, s, cb_index(g, x, y, zm, t), z == 0, acc);
-    hop<SP, GP, 3, +1>(A, in_q, inn_q, p, s, cb_index(g, x, y, z, tp), tp == 0, acc);
-    hop<SP, GP, 3, -1>(A, in_q, inn_q, p, s, cb_index(g, x, y, z, tm), t == 0, acc);
+    // neighbour index computed at its hop (short live ranges); the flag marks a boundary crossing
+    hop<SP, GP, 0, +1>(A, in_q, inn_q, p, s, cb_neighbour<0>(g, s, c), c[0] + 1 == g.L[0], acc);
+    hop<SP, GP, 0, -1>(A, in_q, inn_q, p, s, cb_neighbour<1>(g, s, c), c[0] == 0, acc);
+    hop<SP, GP, 1, +1>(A, in_q, inn_q, p, s, cb_neighbour<2>(g, s, c), c[1] + 1 == g.L[1], acc);
+    hop<SP, GP, 1, -1>(A, in_q, inn_q, p, s, cb_neighbour<3>(g, s, c), c[1] == 0, acc);
+    hop<SP, GP, 2, +1>(A, in_q, inn_q, p, s, cb_neighbour<4>(g, s, c), c[2] + 1 == g.L[2], acc);
+    hop<SP, GP, 2, -1>(A, in_q, inn_q, p, s, cb_neighbour<5>(g, s, c), c[2] == 0, acc);
+    hop<SP, GP, 3, +1>(A, in_q, inn_q, p, s, cb_neighbour<6>(g, s, c), c[3] + 1 == g.L[3], acc);
+    hop<SP, GP, 3, -1>(A, in_q, inn_q, p, s, cb_neighbour<7>(g, s, c), c[3] == 0, acc);
 
     epilogue<SP, NY>(A, r, p, s, acc);
 }
@@ -393,14 +388,12 @@ __global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
     const float* inn_q = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
     int c[4];
     cb_coords(g, s, p, c);
-    const int x = c[0], y = c[1], z = c[2], t = c[3];
-    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
-    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
-    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
-    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
-    const int sn[8] = {cb_index(g, xp, y, z, t), cb_index(g, xm, y, z, t), cb_index(g, x, yp, z, t),
-                       cb_index(g, x, ym, z, t), cb_index(g, x, y, zp, t), cb_index(g, x, y, zm, t),
-                       cb_index(g, x, y, z, tp), cb_index(g, x, y, z, tm)};
+    int nbr[8];
+    cb_neighbours(g, s, c, nbr);
+    // hops crossing the lattice boundary (they carry the boundary phase)
+    const bool xp0 = c[0] + 1 == g.L[0], xm0 = c[0] == 0, yp0 = c[1] + 1 == g.L[1], ym0 = c[1] == 0;
+    const bool zp0 = c[2] + 1 == g.L[2], zm0 = c[2] == 0, tp0 = c[3] + 1 == g.L[3], tm0 = c[3] == 0;
+    const int* sn = nbr;
     constexpr size_t LB = gauge_link_bytes_dev<GP>();
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
@@ -412,14 +405,14 @@ __global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
     float acc[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp == 0, (float)g.bc[0], acc);
-    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, x == 0, (float)g.bc[0], acc);
-    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp == 0, (float)g.bc[1], acc);
-    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, y == 0, (float)g.bc[1], acc);
-    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp == 0, (float)g.bc[2], acc);
-    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, z == 0, (float)g.bc[2], acc);
-    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp == 0, (float)g.bc[3], acc);
-    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, t == 0, (float)g.bc[3], acc);
+    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp0, (float)g.bc[0], acc);
+    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, xm0, (float)g.bc[0], acc);
+    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp0, (float)g.bc[1], acc);
+    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, ym0, (float)g.bc[1], acc);
+    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp0, (float)g.bc[2], acc);
+    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, zm0, (float)g.bc[2], acc);
+    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp0, (float)g.bc[3], acc);
+    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, tm0, (float)g.bc[3], acc);
     epilogue<SP, NY>(A, r, p, s, acc);
 }
 
@@ -643,14 +636,12 @@ __global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashA
     const int s = s0 + threadIdx.x;
     int c[4] = {0, 0, 0, 0};
     if (s < g.Vh) cb_coords(g, s, p, c);
-    const int x = c[0], y = c[1], z = c[2], t = c[3];
-    const int xp = x + 1 == g.L[0] ? 0 : x + 1, xm = x == 0 ? g.L[0] - 1 : x - 1;
-    const int yp = y + 1 == g.L[1] ? 0 : y + 1, ym = y == 0 ? g.L[1] - 1 : y - 1;
-    const int zp = z + 1 == g.L[2] ? 0 : z + 1, zm = z == 0 ? g.L[2] - 1 : z - 1;
-    const int tp = t + 1 == g.L[3] ? 0 : t + 1, tm = t == 0 ? g.L[3] - 1 : t - 1;
-    const int nb[8] = {cb_index(g, xp, y, z, t), cb_index(g, xm, y, z, t), cb_index(g, x, yp, z, t),
-                       cb_index(g, x, ym, z, t), cb_index(g, x, y, zp, t), cb_index(g, x, y, zm, t),
-                       cb_index(g, x, y, z, tp), cb_index(g, x, y, z, tm)};
+    int nbr[8];
+    cb_neighbours(g, s, c, nbr);
+    // hops crossing the lattice boundary (they carry the boundary phase)
+    const bool xp0 = c[0] + 1 == g.L[0], xm0 = c[0] == 0, yp0 = c[1] + 1 == g.L[1], ym0 = c[1] == 0;
+    const bool zp0 = c[2] + 1 == g.L[2], zm0 = c[2] == 0, tp0 = c[3] + 1 == g.L[3], tm0 = c[3] == 0;
+    const int* nb = nbr;
     float lk[PRE ? 8 : 1][12];
     if constexpr (PRE) {
         if (s < g.Vh) {
@@ -698,14 +689,14 @@ __global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashA
     float acc[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_tma<SP, GP, 0, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[0], xp == 0, lk[0], acc);
-    hop_tma<SP, GP, 0, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[1], x == 0, lk[PRE ? 1 : 0], acc);
-    hop_tma<SP, GP, 1, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[2], yp == 0, lk[PRE ? 2 : 0], acc);
-    hop_tma<SP, GP, 1, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[3], y == 0, lk[PRE ? 3 : 0], acc);
-    hop_tma<SP, GP, 2, +1, PRE>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, nb[4], zp == 0, lk[PRE ? 4 : 0], acc);
-    hop_tma<SP, GP, 2, -1, PRE>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, nb[5], z == 0, lk[PRE ? 5 : 0], acc);
-    hop_tma<SP, GP, 3, +1, PRE>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, nb[6], tp == 0, lk[PRE ? 6 : 0], acc);
-    hop_tma<SP, GP, 3, -1, PRE>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, nb[7], t == 0, lk[PRE ? 7 : 0], acc);
+    hop_tma<SP, GP, 0, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[0], xp0, lk[0], acc);
+    hop_tma<SP, GP, 0, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[1], xm0, lk[PRE ? 1 : 0], acc);
+    hop_tma<SP, GP, 1, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[2], yp0, lk[PRE ? 2 : 0], acc);
+    hop_tma<SP, GP, 1, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[3], ym0, lk[PRE ? 3 : 0], acc);
+    hop_tma<SP, GP, 2, +1, PRE>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, nb[4], zp0, lk[PRE ? 4 : 0], acc);
+    hop_tma<SP, GP, 2, -1, PRE>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, nb[5], zm0, lk[PRE ? 5 : 0], acc);
+    hop_tma<SP, GP, 3, +1, PRE>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, nb[6], tp0, lk[PRE ? 6 : 0], acc);
+    hop_tma<SP, GP, 3, -1, PRE>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, nb[7], tm0, lk[PRE ? 7 : 0], acc);
     epilogue<SP, NY>(A, r, p, s, acc);
 }
 

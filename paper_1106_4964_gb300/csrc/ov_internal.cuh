@@ -114,11 +114,36 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
+// Division of a non-negative 31-bit integer by a divisor fixed at set-up, by one
+// high multiply, an add and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994, Thm. 4.2 with N = 32):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (mulhi(m, n) + n) >> l.
+// mulhi(m, n) < n, so the sum stays below 2^32 for n < 2^31.
+struct FastDiv {
+    uint32_t d, m, l;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div), m(0), l(0)
+    {
+        while ((1ull << l) < div) ++l;
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+    }
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const
+    {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi = __umulhi(m, n);
+#else
+        const uint32_t hi = (uint32_t)(((uint64_t)m * n) >> 32);
+#endif
+        return (hi + n) >> l;
+    }
+};
+
 struct Geom {
     int L[4];   // Lx, Ly, Lz, Lt
     int Lxh;    // Lx / 2
     int Vh;     // sites per parity
     double bc[4];
+    FastDiv fxh, fy, fz;  // division by Lxh, Ly, Lz
 };
 
 // A field of nrhs right-hand sides in the internal layout of one precision.
@@ -139,18 +164,53 @@ struct FieldDesc {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cb_coords(const Geom& g, int s, int p, int c[4])
 {
-    int xh = s % g.Lxh;
-    int r = s / g.Lxh;
-    c[1] = r % g.L[1];
-    r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
+    const uint32_t r0 = g.fxh.div((uint32_t)s);
+    const int xh = s - (int)r0 * g.Lxh;
+    const uint32_t r1 = g.fy.div(r0);
+    c[1] = (int)(r0 - r1 * (uint32_t)g.L[1]);
+    const uint32_t r2 = g.fz.div(r1);
+    c[2] = (int)(r1 - r2 * (uint32_t)g.L[2]);
+    c[3] = (int)r2;
     c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
 }
 
 __device__ __forceinline__ int cb_index(const Geom& g, int x, int y, int z, int t)
 {
     return ((t * g.L[2] + z) * g.L[1] + y) * g.Lxh + (x >> 1);
+}
+
+// Checkerboard indices of the eight neighbours of site s (coordinates c), in the
+// order +x, -x, +y, -y, +z, -z, +t, -t, as offsets from s: both parities number
+// their sites the same way, so a y, z or t hop is a fixed shift (with the
+// periodic wrap), and an x hop stays in the row of s.
+template <int H>
+__device__ __forceinline__ int cb_neighbour(const Geom& g, int s, const int c[4])
+{
+    const int dy = g.Lxh, dz = g.Lxh * g.L[1], dt = dz * g.L[2];
+    if constexpr (H == 0) return s - (c[0] >> 1) + ((c[0] + 1 == g.L[0] ? 0 : c[0] + 1) >> 1);
+    if constexpr (H == 1) return s - (c[0] >> 1) + ((c[0] == 0 ? g.L[0] - 1 : c[0] - 1) >> 1);
+    if constexpr (H == 2) return c[1] + 1 == g.L[1] ? s - (g.L[1] - 1) * dy : s + dy;
+    if constexpr (H == 3) return c[1] == 0 ? s + (g.L[1] - 1) * dy : s - dy;
+    if constexpr (H == 4) return c[2] + 1 == g.L[2] ? s - (g.L[2] - 1) * dz : s + dz;
+    if constexpr (H == 5) return c[2] == 0 ? s + (g.L[2] - 1) * dz : s - dz;
+    if constexpr (H == 6) return c[3] + 1 == g.L[3] ? s - (g.L[3] - 1) * dt : s + dt;
+    return c[3] == 0 ? s + (g.L[3] - 1) * dt : s - dt;
+}
+
+__device__ __forceinline__ void cb_neighbours(const Geom& g, int s, const int c[4], int nb[8])
+{
+    const int row = s - (c[0] >> 1);
+    const int xp = c[0] + 1 == g.L[0] ? 0 : c[0] + 1;
+    const int xm = c[0] == 0 ? g.L[0] - 1 : c[0] - 1;
+    nb[0] = row + (xp >> 1);
+    nb[1] = row + (xm >> 1);
+    const int dy = g.Lxh, dz = g.Lxh * g.L[1], dt = dz * g.L[2];
+    nb[2] = c[1] + 1 == g.L[1] ? s - (g.L[1] - 1) * dy : s + dy;
+    nb[3] = c[1] == 0 ? s + (g.L[1] - 1) * dy : s - dy;
+    nb[4] = c[2] + 1 == g.L[2] ? s - (g.L[2] - 1) * dz : s + dz;
+    nb[5] = c[2] == 0 ? s + (g.L[2] - 1) * dz : s - dz;
+    nb[6] = c[3] + 1 == g.L[3] ? s - (g.L[3] - 1) * dt : s + dt;
+    nb[7] = c[3] == 0 ? s + (g.L[3] - 1) * dt : s - dt;
 }
 
 // ---------------------------------------------------------------------------

@@ -2,12 +2,15 @@
 include/overlap.h declares; the Python binding covers each of them.  No
 compute call is made (no GPU here)."""
 import ctypes
+import os
 import subprocess
 
 import pytest
 
 from paper_1106_4964_gb300 import binding
 from paper_1106_4964_gb300 import build as b
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -52,3 +55,20 @@ def _fresh_load(path):
         binding.load(path)
     finally:
         binding._lib = saved
+
+
+def test_fast_division_host_side(tmp_path):
+    """The invariant-divisor division behind the device coordinate maps, compiled for the host
+    and compared with integer division on dense and random numerators below 2^31."""
+    import shutil
+    import subprocess
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "fastdiv")
+    csrc = os.path.join(ROOT, "paper_1106_4964_gb300", "csrc")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-I", csrc, "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "fastdiv_check.cu"), "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
