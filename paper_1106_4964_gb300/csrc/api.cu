@@ -1012,9 +1012,10 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
 {
     if (!c) return OV_EINVAL;
     OV_TRY(check_prec(c, prec));
-    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant >= 3 && (wide(prec) || by != 1)))
+    if (variant < 0 || variant >= DSLASH_VARIANTS || (variant >= 3 && wide(prec)) ||
+        ((variant == 3 || variant == 4 || variant == 5) && by != 1))
         return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
-    const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 ? 128 : 256);
+    const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 || variant >= 6 ? 128 : 256);
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
     c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
@@ -1036,8 +1037,17 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
     std::vector<std::tuple<int, int, int>> cand;
     for (int v = 0; v < DSLASH_VARIANTS; ++v) {
         if (v >= 3 && wide(prec)) continue;  // staged variants: FP32 arithmetic only
-        if (v >= 4) {                        // bulk-copy staging: fixed 128-site blocks
+        if (v == 4 || v == 5) {              // bulk-copy staging: fixed 128-site blocks
             cand.push_back(std::make_tuple(128, 1, v));
+            continue;
+        }
+        if (v >= 6) {                        // 2 or 4 right-hand sides per thread
+            const int rb = v == 6 ? 2 : 4;
+            if (nrhs < rb) continue;
+            const int groups = (nrhs + rb - 1) / rb;
+            for (int x : {32, 64, 128})
+                for (int y = 1; y <= groups && x * y <= 128; ++y)
+                    if (groups % y == 0 && x * y >= 64) cand.push_back(std::make_tuple(x, y, v));
             continue;
         }
         const int maxt = v == 0 ? (wide(prec) ? 256 : 512) : (v == 3 ? 128 : 256);
