@@ -375,8 +375,8 @@ def _events(torch):
 
 
 def run_overlap(args):
-    """Overlap application on 24^3 x 64 (rho 1.5): the lowest nev H_w modes deflated (Lanczos on
-    T_100(H_w^2), FP32 filter, FP64 Gram-Schmidt and Rayleigh-Ritz), degree-n Chebyshev on the rest,
+    """Overlap application on 24^3 x 64 (rho 1.5): the lowest nev H_w modes deflated (subspace
+    iteration on T_100(H_w^2), FP32 filter, FP64 Gram-Schmidt and Rayleigh-Ritz), degree-n Chebyshev on the rest,
     eps = (0.99 |lambda_nev| / lambda_max)^2.  Times one application per precision (1 and 12 rhs)
     and reports each precision's error against the FP64 application."""
     import torch

@@ -120,11 +120,12 @@ int ov_get_sign_poly(const ov_ctx* ctx, double* rho, double* eps, int* degree, d
 int ov_apply_overlap(ov_ctx* ctx, const void* in, void* out, double mass, int nrhs, int prec, void* stream);
 
 /* Compute and store eigenpairs (Sec. V: eigensolvers for H_w and D).
- * which = 0: the nev eigenpairs of H_w with smallest |lambda| (Lanczos on a
- *            Chebyshev filter of H_w^2, FP64 Gram-Schmidt, Rayleigh-Ritz of
- *            H_w for the signed eigenvalues); they deflate the sign (Eq. 7).
- * which = 1: the nev smallest eigenpairs of D(0)^dag D(0) (Lanczos with FP64
- *            Gram-Schmidt); they deflate the CG (Eq. 9).
+ * which = 0: the nev eigenpairs of H_w with smallest |lambda| (subspace
+ *            iteration with a Chebyshev filter of H_w^2, FP64 Gram-Schmidt,
+ *            Rayleigh-Ritz of H_w for the signed eigenvalues); they deflate
+ *            the sign (Eq. 7).
+ * which = 1: the nev smallest eigenpairs of D(0)^dag D(0) (the same method per
+ *            chiral sector); they deflate the CG (Eq. 9).
  * tol: relative eigen-residual target.  Returns OV_ENOTCONV if not reached. */
 int ov_deflate(ov_ctx* ctx, int which, int nev, double tol, void* stream);
 /* Install eigenpairs computed elsewhere: vals[nev] (signed eigenvalues of H_w

@@ -1,5 +1,5 @@
 // C ABI of the library: context, gauge packing, dslash / H_w / overlap
-// application, internal-layout fields.  The solvers (Lanczos, CG) live in
+// application, internal-layout fields.  The solvers (eigensolver, CG) live in
 // solver.cu, the learned preconditioner in net.cu.
 #include <cmath>
 #include <cstdlib>

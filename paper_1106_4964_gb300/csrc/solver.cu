@@ -1,12 +1,13 @@
 // Solvers of the hot path, host logic over the library's kernels:
 //  * estimate_lambda_max: Lanczos on H_w^2 for ||H_w|| (the spectral rescale Q = H_w / ||H_w||, Eq. 5);
-//  * deflate_impl: thick-restart Lanczos with full FP64 Gram-Schmidt (CGS2), on a Chebyshev filter
-//    T_K(Y(A)) of A = H_w^2 (Sec. V: Chebyshev acceleration, eigenvectors of T_n(H_w^2)) or of
-//    A = D^dag D, then Rayleigh-Ritz in the converged subspace (signed eigenvalues of H_w for Eq. 7);
+//  * deflate_impl: Chebyshev-filtered subspace iteration with full FP64 Gram-Schmidt (CGS2): a block
+//    filtered by T_K(Y(A)) of A = H_w^2 (Sec. V: Chebyshev acceleration, eigenvectors of T_n(H_w^2))
+//    or of A = D^dag D, Rayleigh-Ritz with A every sweep, the filter's cut following the block's Ritz
+//    values, then Rayleigh-Ritz with H_w for the signed eigenvalues of Eq. 7;
 //  * cg_impl: deflated CG on D(m)^dag D(m) (Eq. 9) with mixed precision and FP64 reliable updates,
 //    optionally preconditioned by the learned network (flexible CG, net.cu).
-// The paper uses implicitly restarted Arnoldi; the operators here are Hermitian, so the Lanczos form
-// of the same restarted Krylov method is used (k = l + dl basis vectors, Sec. V).
+// The paper uses implicitly restarted Arnoldi on the filtered operator; the operators here are
+// Hermitian, and a filtered block iteration lets the filter interval adapt between sweeps.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -305,23 +306,27 @@ int project_chiral(ov_ctx* c, const FieldDesc& v, int chi, cudaStream_t st)
 }
 
 struct LanczosWork {
-    FieldDesc basis, rot, Z, zero, w, tmp[4];
+    FieldDesc basis, rot, zero, w, tmp[4];
 };
 
-// Thick-restart Lanczos for the nev smallest eigenvalues of the Hermitian A on the
-// chirality-chi subspace (chi = 0: whole space; +-1: gamma5 = chi, enforced after
-// every operator application), accelerated by the Chebyshev filter T_K(Y(A)) on
-// [acut, bmax] whose cutoff comes from an unfiltered Lanczos run (its j-th Ritz value
-// bounds the j-th eigenvalue from above).  Converged Ritz vectors are refined by
-// Rayleigh-Ritz with R; the result is accepted when max_i |R eta_i - lam_i eta_i| <=
-// tol * rscale.  Vectors go to `out` (nev fields), values (sorted by |lam|) to vals.
-int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, double bmax, int nev, int m, int kkeep,
-          double tol, double rscale, int chi, unsigned long long seed, LanczosWork& W, std::vector<double>& vals,
-          const FieldDesc& out, double* maxres_out, cudaStream_t st)
+// Chebyshev-filtered subspace iteration for the nev smallest eigenpairs of the Hermitian A on
+// the chirality-chi subspace (chi = 0: whole space; +-1: gamma5 = chi, enforced after every
+// operator application).  A block of nb orthonormal FP64 vectors is filtered with T_K(Y(A)) on
+// [acut, bmax] (work-precision fields), re-orthonormalised by CGS2 and Rayleigh-Ritz-projected
+// with A.  The cut starts at an upper bound of the eigenvalue of index nb from a short
+// unfiltered Lanczos run (Ritz values bound the eigenvalues of the same index from above) and
+// then follows the largest Ritz value of the block, also an upper bound of that eigenvalue
+// (Courant-Fischer), so the filter sharpens as the block converges.  Leading Ritz vectors whose
+// A-residual is small enough are locked (no longer filtered).  Finally the nev leading vectors
+// are rotated by Rayleigh-Ritz with R and accepted when max_i |R eta_i - lam_i eta_i| <=
+// tol * rscale.  sq: A = R^2 (an R-residual e shows as about 2 |lam| e in A).  Vectors go to
+// `out` (nev fields), values (sorted by |lam|) to vals.
+int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, double bmax, int nev, int nb,
+          double tol, double rscale, bool sq, int chi, unsigned long long seed, LanczosWork& W,
+          std::vector<double>& vals, const FieldDesc& out, double* maxres_out, cudaStream_t st)
 {
     int status = OV_OK;
-    const FieldDesc& basis = W.basis;
-    // A on FP64 fields (unfiltered run) and Awork on fields of the filter's work precision
+    const FieldDesc& V = W.basis;
     OpFn Ac = [&](const FieldDesc& in, const FieldDesc& o) -> int {
         OV_TRY(A(in, o));
         return project_chiral(c, o, chi, st);
@@ -330,126 +335,147 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         OV_TRY(Awork(in, o));
         return project_chiral(c, o, chi, st);
     };
-    // cutoff from an unfiltered run
-    std::vector<double> ritz0;
+    // normalised w -> V_j after CGS2 against V[0..j); a random vector replaces a vanishing one
+    auto orth_into = [&](int j, unsigned long long s) -> int {
+        for (int attempt = 0; attempt < 3; ++attempt) {
+            std::vector<cd> h;
+            if (j > 0) OV_TRY(cgs2(c, V, j, W.w, h, st));
+            const double nr = host_norm(c, W.w, st, &status);
+            OV_TRY(status);
+            if (nr > 1e-200) return scale_into(c, W.w, sub(V, j), 1.0 / nr, st);
+            OV_CUDA(c, launch_fill_random(c->g, W.w, s + 7919ull * (attempt + 1), st));
+            OV_TRY(project_chiral(c, W.w, chi, st));
+        }
+        return set_err(c, OV_ENOTCONV, "eigensolver: block vector %d vanished", j);
+    };
+
+    // cut: upper bound of lambda_{nb} from an unfiltered Lanczos run
+    double acut;
     {
-        const int m0 = std::min(m, std::max(2 * nev + 20, 40));
-        OV_CUDA(c, launch_fill_random(c->g, sub(basis, 0), seed + 101, st));
-        OV_TRY(project_chiral(c, sub(basis, 0), chi, st));
-        double nr = host_norm(c, sub(basis, 0), st, &status);
+        const int m0 = std::min(V.nrhs - 1, nb + 40);
+        OV_CUDA(c, launch_fill_random(c->g, sub(V, 0), seed + 101, st));
+        OV_TRY(project_chiral(c, sub(V, 0), chi, st));
+        double nr = host_norm(c, sub(V, 0), st, &status);
         OV_TRY(status);
-        OV_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
+        OV_TRY(scale_into(c, sub(V, 0), sub(V, 0), 1.0 / nr, st));
         std::vector<cd> T((size_t)m0 * m0, cd(0, 0));
         int mm = m0;
         for (int j = 0; j < m0; ++j) {
-            OV_TRY(Ac(sub(basis, j), W.w));
+            OV_TRY(Ac(sub(V, j), W.w));
             std::vector<cd> h;
-            OV_TRY(cgs2(c, basis, j + 1, W.w, h, st));
+            OV_TRY(cgs2(c, V, j + 1, W.w, h, st));
             for (int i = 0; i <= j; ++i) {
                 T[(size_t)i * m0 + j] = h[i];
                 T[(size_t)j * m0 + i] = std::conj(h[i]);
             }
-            double beta = host_norm(c, W.w, st, &status);
+            const double beta = host_norm(c, W.w, st, &status);
             OV_TRY(status);
             if (j + 1 < m0) {
                 if (beta < 1e-12 * std::abs(T[(size_t)j * m0 + j]) + 1e-300) {
                     mm = j + 1;
                     break;
                 }
-                OV_TRY(scale_into(c, W.w, sub(basis, j + 1), 1.0 / beta, st));
+                OV_TRY(scale_into(c, W.w, sub(V, j + 1), 1.0 / beta, st));
             }
         }
         std::vector<cd> Tm((size_t)mm * mm), Zt;
         for (int i = 0; i < mm; ++i)
             for (int j = 0; j < mm; ++j) Tm[(size_t)i * mm + j] = T[(size_t)i * m0 + j];
+        std::vector<double> ritz0;
         herm_eig(mm, Tm, ritz0, Zt);
+        acut = ritz0[std::min((int)ritz0.size() - 1, nb - 1)];
+        if (!(acut < bmax)) acut = 0.5 * bmax;
     }
-    const int jcut = std::min((int)ritz0.size() - 1, nev + std::max(4, nev / 2));
-    double acut = ritz0[jcut];
-    if (!(acut < bmax)) acut = 0.5 * bmax;
-    // Cap the degree so that the filter's dynamic range, bounded by T_K at x = 0, stays within what
-    // the work precision resolves: otherwise rounding relative to the largest filtered eigenvalue
-    // swamps the smaller wanted ones (1e12 for FP64 work fields, 1e4 for FP32).
-    int Keff = K;
-    if (K > 0) {
+    // random orthonormal block
+    for (int j = 0; j < nb; ++j) {
+        OV_CUDA(c, launch_fill_random(c->g, W.w, seed + 1000003ull * (j + 1), st));
+        OV_TRY(project_chiral(c, W.w, chi, st));
+        OV_TRY(orth_into(j, seed + j));
+    }
+
+    std::vector<double> theta(nb, 0.0), res(nb, 1e300);
+    int nlock = 0;
+    double tscale = 1.0;  // tightens the locking threshold when the final R check fails
+    auto tolA = [&](double th) {
+        return tscale * (sq ? tol * rscale * std::sqrt(std::max(th, 0.0)) : 0.5 * tol * rscale);
+    };
+    double maxres = 1e300;
+    for (int it = 0; it < 300; ++it) {
+        // degree: even (T_K > 0 below the cut) and capped so that T_K(0) stays within what the work
+        // precision resolves (1e12 FP64, 1e10 double-float, 1e4 FP32)
         const double y0 = (bmax + acut) / (bmax - acut);
         const double limit = W.tmp[0].prec == P_F64 ? 1e12 : (W.tmp[0].prec == P_DF64 ? 1e10 : 1e4);
         const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
-        // even degree: T_K is then positive below the cutoff, so the wanted eigenvalues are the
-        // largest of the filter (an odd degree would send them to large negative values)
-        Keff = std::max(2, std::min(K, kmax)) & ~1;
-    }
-    if (verbose())
-        fprintf(stderr, "[ov] lanczos chi=%d nev=%d m=%d: cut %.4e of %.4e, filter degree %d (asked %d)\n", chi, nev,
-                m, acut, bmax, Keff, K);
-    OpFn F = [&](const FieldDesc& in, const FieldDesc& o) -> int {
-        OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, in, o, W.tmp, st));
-        return project_chiral(c, o, chi, st);
-    };
-
-    OV_CUDA(c, launch_fill_random(c->g, sub(basis, 0), seed, st));
-    OV_TRY(project_chiral(c, sub(basis, 0), chi, st));
-    {
-        double nr = host_norm(c, sub(basis, 0), st, &status);
-        OV_TRY(status);
-        OV_TRY(scale_into(c, sub(basis, 0), sub(basis, 0), 1.0 / nr, st));
-    }
-    std::vector<cd> T((size_t)m * m, cd(0, 0));
-    std::vector<double> theta;
-    std::vector<cd> Y;
-    std::vector<int> order(m);
-    int k = 0;
-    double tolF = tol;
-    double maxres = 1e300;
-    for (int restart = 0; restart < 300; ++restart) {
-        double beta = 0;
-        for (int j = k; j < m; ++j) {
-            OV_TRY(F(sub(basis, j), W.w));
-            std::vector<cd> h;
-            OV_TRY(cgs2(c, basis, j + 1, W.w, h, st));
-            for (int i = 0; i <= j; ++i) {
-                T[(size_t)i * m + j] = h[i];
-                T[(size_t)j * m + i] = std::conj(h[i]);
+        const int Keff = std::max(2, std::min(K, kmax)) & ~1;
+        for (int j = nlock; j < nb; ++j) {
+            OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, sub(V, j), W.w, W.tmp, st));
+            OV_TRY(project_chiral(c, W.w, chi, st));
+            OV_TRY(orth_into(j, seed + 31ull * it + j));
+        }
+        // Rayleigh-Ritz with A over the block (locked vectors keep their Ritz values)
+        std::vector<cd> G((size_t)nb * nb, cd(0, 0));
+        for (int j = nlock; j < nb; ++j) {
+            OV_TRY(Ac(sub(V, j), W.w));
+            OV_TRY(block_dots(c, V, nb, W.w, st));
+            std::vector<double2> hh(nb);
+            OV_TRY(to_host(c, c->dscal, hh.data(), nb * sizeof(double2), st));
+            for (int i = 0; i < nb; ++i) G[(size_t)i * nb + j] = cd(hh[i].x, hh[i].y);
+        }
+        for (int i = 0; i < nb; ++i) {
+            if (i < nlock) {
+                G[(size_t)i * nb + i] = theta[i];
+                for (int j = nlock; j < nb; ++j) G[(size_t)j * nb + i] = std::conj(G[(size_t)i * nb + j]);
+                continue;
             }
-            T[(size_t)j * m + j] = h[j].real();
-            beta = host_norm(c, W.w, st, &status);
+            for (int j = i; j < nb; ++j) {
+                const cd a = 0.5 * (G[(size_t)i * nb + j] + std::conj(G[(size_t)j * nb + i]));
+                G[(size_t)i * nb + j] = a;
+                G[(size_t)j * nb + i] = std::conj(a);
+            }
+        }
+        std::vector<double> th;
+        std::vector<cd> S;
+        herm_eig(nb, G, th, S);
+        OV_TRY(rotate(c, V, nb, S, nb, nb, W.rot, W.zero, st));
+        OV_CUDA(c, cudaMemcpyAsync(V.data, W.rot.data, V.rhs_bytes() * nb, cudaMemcpyDeviceToDevice, st));
+        theta = th;
+        // residuals of the wanted Ritz pairs beyond the locked ones; lock the leading converged ones
+        nlock = 0;
+        for (int j = 0; j < nev; ++j) {
+            if (j == nlock && res[j] <= tolA(theta[j]) * 0.5) {
+                ++nlock;  // was converged before this rotation by a margin: keep it locked
+                continue;
+            }
+            OV_TRY(Ac(sub(V, j), W.w));
+            FieldDesc xs[2] = {W.w, sub(V, j)};
+            const double2 h2[2] = {make_double2(1, 0), make_double2(-theta[j], 0)};
+            OV_TRY(lincomb(c, W.w, 2, xs, h2, nullptr, 0, nullptr, st));
+            res[j] = host_norm(c, W.w, st, &status);
             OV_TRY(status);
-            if (beta < 1e-300) beta = 1e-300;
-            OV_TRY(scale_into(c, W.w, sub(basis, j + 1), 1.0 / beta, st));
+            if (j == nlock && res[j] <= tolA(theta[j])) ++nlock;
         }
-        std::vector<cd> Tc = T;
-        herm_eig(m, Tc, theta, Y);
-        for (int i = 0; i < m; ++i) order[i] = m - 1 - i;  // largest of F first
-        int nconv = 0;
-        for (int i = 0; i < nev; ++i) {
-            const double r = beta * std::abs(Y[(size_t)(m - 1) * m + order[i]]);
-            if (r <= tolF * std::fabs(theta[order[i]])) ++nconv;
-        }
-        // Rayleigh-Ritz when the filter's Ritz pairs look converged, and every 4th restart anyway
-        // (the filter residuals are pessimistic for the smaller wanted filter values)
-        if (nconv == nev || restart % 4 == 3) {
-            // Rayleigh-Ritz with R in the span of the nev leading Ritz vectors (basis untouched)
-            std::vector<cd> Yk((size_t)m * nev);
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j < nev; ++j) Yk[(size_t)i * nev + j] = Y[(size_t)i * m + order[j]];
-            OV_TRY(rotate(c, basis, m, Yk, nev, nev, W.Z, W.zero, st));
+        if (verbose())
+            fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d/%d, res[nev-1] %.3e\n", chi, it,
+                    acut, Keff, nlock, nev, res[nev - 1]);
+        if (nlock >= nev) {
+            // Rayleigh-Ritz with R on the nev leading vectors (splits the +-lambda pairs of R^2)
             std::vector<cd> M((size_t)nev * nev);
             for (int j = 0; j < nev; ++j) {
-                OV_TRY(R(sub(W.Z, j), W.w));
-                OV_TRY(block_dots(c, W.Z, nev, W.w, st));
+                OV_TRY(R(sub(V, j), W.w));
+                OV_TRY(block_dots(c, V, nev, W.w, st));
                 std::vector<double2> hh(nev);
                 OV_TRY(to_host(c, c->dscal, hh.data(), nev * sizeof(double2), st));
                 for (int i = 0; i < nev; ++i) M[(size_t)i * nev + j] = cd(hh[i].x, hh[i].y);
             }
             for (int i = 0; i < nev; ++i)
                 for (int j = i; j < nev; ++j) {
-                    cd a = 0.5 * (M[(size_t)i * nev + j] + std::conj(M[(size_t)j * nev + i]));
+                    const cd a = 0.5 * (M[(size_t)i * nev + j] + std::conj(M[(size_t)j * nev + i]));
                     M[(size_t)i * nev + j] = a;
                     M[(size_t)j * nev + i] = std::conj(a);
                 }
             std::vector<double> lam;
-            std::vector<cd> S;
-            herm_eig(nev, M, lam, S);
+            std::vector<cd> Sr;
+            herm_eig(nev, M, lam, Sr);
             std::vector<int> o(nev);
             for (int i = 0; i < nev; ++i) o[i] = i;
             std::sort(o.begin(), o.end(), [&](int a, int b) { return std::fabs(lam[a]) < std::fabs(lam[b]); });
@@ -457,23 +483,21 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             std::vector<double> lo(nev);
             for (int j = 0; j < nev; ++j) {
                 lo[j] = lam[o[j]];
-                for (int i = 0; i < nev; ++i) So[(size_t)i * nev + j] = S[(size_t)i * nev + o[j]];
+                for (int i = 0; i < nev; ++i) So[(size_t)i * nev + j] = Sr[(size_t)i * nev + o[j]];
             }
             FieldDesc eta = sub(W.rot, 0, nev);
-            OV_TRY(rotate(c, W.Z, nev, So, nev, nev, eta, W.zero, st));
+            OV_TRY(rotate(c, V, nev, So, nev, nev, eta, W.zero, st));
             maxres = 0;
             for (int j = 0; j < nev; ++j) {
                 OV_TRY(R(sub(eta, j), W.w));
                 FieldDesc xs[2] = {W.w, sub(eta, j)};
-                double2 h[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
-                OV_TRY(lincomb(c, W.w, 2, xs, h, nullptr, 0, nullptr, st));
+                const double2 h2[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
+                OV_TRY(lincomb(c, W.w, 2, xs, h2, nullptr, 0, nullptr, st));
                 const double r = host_norm(c, W.w, st, &status);
                 OV_TRY(status);
                 maxres = std::max(maxres, r / rscale);
             }
-            if (verbose())
-                fprintf(stderr, "[ov] lanczos restart %d: %d/%d filter pairs converged, max eigen-residual %.3e\n",
-                        restart, nconv, nev, maxres);
+            if (verbose()) fprintf(stderr, "[ov] chfsi chi=%d: Rayleigh-Ritz max eigen-residual %.3e\n", chi, maxres);
             if (maxres <= tol) {
                 OV_CUDA(c, cudaMemcpyAsync(out.data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
                 OV_CUDA(c, cudaStreamSynchronize(st));
@@ -481,22 +505,14 @@ int trlan(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            if (nconv == nev) tolF = std::max(tolF * 1e-2, 1e-15);  // Ritz pairs of F need more accuracy
+            tscale *= 0.1;  // the A-residual threshold was too loose for the R criterion
+            nlock = 0;
+            std::fill(res.begin(), res.end(), 1e300);
         }
-        // thick restart with the kkeep leading Ritz vectors
-        std::vector<cd> Yk((size_t)m * kkeep);
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < kkeep; ++j) Yk[(size_t)i * kkeep + j] = Y[(size_t)i * m + order[j]];
-        OV_TRY(rotate(c, basis, m, Yk, kkeep, kkeep, W.rot, W.zero, st));
-        OV_CUDA(c, cudaMemcpyAsync(basis.data, W.rot.data, W.rot.rhs_bytes() * kkeep, cudaMemcpyDeviceToDevice, st));
-        OV_CUDA(c, cudaMemcpyAsync(sub(basis, kkeep).data, sub(basis, m).data, basis.rhs_bytes(),
-                                   cudaMemcpyDeviceToDevice, st));
-        std::fill(T.begin(), T.end(), cd(0, 0));
-        for (int i = 0; i < kkeep; ++i) T[(size_t)i * m + i] = theta[order[i]];
-        k = kkeep;
+        if (theta[nb - 1] > theta[nev - 1] && theta[nb - 1] < acut) acut = theta[nb - 1];
     }
     *maxres_out = maxres;
-    return set_err(c, OV_ENOTCONV, "Lanczos: max relative eigen-residual %.3e > tol %.3e", maxres, tol);
+    return set_err(c, OV_ENOTCONV, "eigensolver: not converged (max eigen-residual %.3e > tol %.3e)", maxres, tol);
 }
 
 int store_eigs(ov_ctx* c, int which, const FieldDesc& vecs, const std::vector<int>& pick,
@@ -525,10 +541,11 @@ int store_eigs(ov_ctx* c, int which, const FieldDesc& vecs, const std::vector<in
 
 }  // namespace
 
-// which = 0: nev smallest-|lambda| eigenpairs of H_w (Lanczos on T_100(Y(H_w^2)), Rayleigh-Ritz with H_w).
+// which = 0: nev smallest-|lambda| eigenpairs of H_w (subspace iteration with the filter T_100(Y(H_w^2)),
+//            Rayleigh-Ritz with H_w).
 // which = 1: nev smallest eigenpairs of D(0)^dag D(0).  It commutes with gamma5 and its eigenvalues
 //            are doubly degenerate across the two chiral sectors (d and d* of D share |d|^2), which a
-//            single-vector Lanczos cannot resolve, so each sector is solved on its own (the chiral
+//            single-vector Krylov method cannot resolve, so each sector is solved on its own (the chiral
 //            structure Sec. V uses) and the lowest nev of the union are kept.
 int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
 {
@@ -537,9 +554,9 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const long long dim = which == 0 ? N : N / 2;
     const int ns = which == 0 ? nev : std::min<long long>(nev / 2 + 4, nev);
     if (ns >= dim / 2) return set_err(c, OV_EINVAL, "nev = %d too large for a lattice of dimension %lld", nev, N);
-    int m = std::max((5 * ns) / 2, ns + 20);
-    m = (int)std::min<long long>(m, dim - 1);
-    const int kkeep = std::min(m - 1, ns + (m - ns) / 3);
+    // block of the filtered subspace iteration, and the unfiltered Lanczos run that sets the first cut
+    const int nb = (int)std::min<long long>(ns + std::max(10, ns / 2), dim / 2);
+    const int m0 = (int)std::min<long long>(nb + 40, dim - 1);
     // operator precision: FP64 when the eigen-residual target needs it; an FP32 filter (FP64
     // Gram-Schmidt and Rayleigh-Ritz) when tol >= 1e-7, or as set by ov_set_option("eig_prec")
     const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : c->hi_prec);
@@ -550,7 +567,6 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         cudaStreamSynchronize(st);
         field_free(c, &W.basis);
         field_free(c, &W.rot);
-        field_free(c, &W.Z);
         field_free(c, &outv);
     };
 #define DF_TRY(x)           \
@@ -561,9 +577,8 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
             return s__;     \
         }                   \
     } while (0)
-    DF_TRY(field_alloc(c, P_F64, m + 1, &W.basis));
-    DF_TRY(field_alloc(c, P_F64, std::max(kkeep, ns), &W.rot));
-    DF_TRY(field_alloc(c, P_F64, ns, &W.Z));
+    DF_TRY(field_alloc(c, P_F64, std::max(nb, m0 + 1), &W.basis));
+    DF_TRY(field_alloc(c, P_F64, nb, &W.rot));
     DF_TRY(field_alloc(c, P_F64, nsec * ns, &outv));
     DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &W.zero));
     DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &W.w));
@@ -639,7 +654,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         }
         std::vector<double> v;
         double mr = 0;
-        DF_TRY(trlan(c, A, Awork, R, K, bmax, ns, m, kkeep, tol, rscale, chi, 4242ull + 17 * which + s, W, v,
+        DF_TRY(chfsi(c, A, Awork, R, K, bmax, ns, nb, tol, rscale, which == 0, chi, 4242ull + 17 * which + s, W, v,
                      sub(outv, s * ns, ns), &mr, st));
         allv.insert(allv.end(), v.begin(), v.end());
         worst = std::max(worst, mr);
@@ -736,13 +751,18 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
         return c->chiral ? chiral_apply(c, in, out, mass, dch, st) : normal_apply(c, in, out, mass, st);
     };
-    // z = M r; in chiral mode projected back onto each right-hand side's sector, z <- (1 + chi gamma5) z / 2
-    // (the network mixes chiralities), so that the search directions stay where the operator acts
+    // In chiral mode every vector of the inner recursion must stay in its right-hand side's sector:
+    // the one-sign operator acts on the other sector as m^2 (plus a coupling back), so rounding-level
+    // components there would grow by ~rho^2/m^2 per cycle.  v <- (1 + chi gamma5) v / 2 after every
+    // true residual and every preconditioner application (the network mixes chiralities).
+    auto sector_project = [&](const FieldDesc& v) -> int {
+        if (!c->chiral) return OV_OK;
+        FieldDesc v2[2] = {v, v};
+        return lincomb(c, v, 2, v2, nullptr, dch + 3 * R, 2, nullptr, st);
+    };
     auto precond_apply = [&]() -> int {
         OV_TRY(net_apply_precond(c, rs, zs, st));
-        if (!c->chiral) return OV_OK;
-        FieldDesc v2[2] = {zs, zs};
-        return lincomb(c, zs, 2, v2, nullptr, dch + 3 * R, 2, nullptr, st);
+        return sector_project(zs);
     };
 
     std::vector<double> rr(R), rr_new(R), rmax(R), res(R, 1.0), rz(R);
@@ -823,6 +843,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     for (int q = 0; q < R; ++q) prev_worst = std::max(prev_worst, res[q]);
     if (!all_done) {
         if (sloppy) OV_TRY(convert(c, r, rs, st));
+        OV_TRY(sector_project(rs));
         OV_CUDA(c, cudaMemsetAsync(xs.data, 0, xs.rhs_bytes() * R, st));
         if (xs.norm) OV_CUDA(c, cudaMemsetAsync(xs.norm, 0, (size_t)2 * xs.Vh * 4 * R, st));
         OV_TRY(sloppy_norms(rs, rr));
@@ -861,7 +882,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
                 if (done[q]) continue;
                 if (!std::isfinite(rr_new[q])) return set_err(c, OV_ENAN, "cg: NaN/Inf in the residual");
                 if (std::sqrt(rr_new[q]) <= tol * bn[q]) trigger = true;
-                if (sloppy && std::sqrt(rr_new[q]) < delta * rmax[q]) trigger = true;
+                if (std::sqrt(rr_new[q]) < delta * rmax[q]) trigger = true;
             }
             bool restart = false;
             if (trigger) {
@@ -891,6 +912,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
                 prev_worst = worst;
                 since = 0;
                 if (sloppy) OV_TRY(convert(c, r, rs, st));
+                OV_TRY(sector_project(rs));
                 OV_TRY(sloppy_norms(rs, rr_new));
                 for (int q = 0; q < R; ++q) rmax[q] = std::sqrt(rr_new[q]);
             }
