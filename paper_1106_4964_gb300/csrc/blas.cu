@@ -110,12 +110,12 @@ __global__ void unpack_kernel(Geom g, const char* data, const float* norm, doubl
 __device__ __forceinline__ void atomic_max_pos(unsigned* a, float v) { atomicMax(a, __float_as_uint(fmaxf(v, 0.f))); }
 
 template <int P>
-__device__ __forceinline__ void store_link(char* base, int Vh, int s, const double u[12])
+__device__ __forceinline__ void store_link(char* base, int Vh, int s, const double u[18])
 {
-    if constexpr (P == P_DF64) {
+    if constexpr (P == P_DF64) {  // all three rows
         float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 9; ++k) {
             const df64 a(u[2 * k]), c(u[2 * k + 1]);
             b[(size_t)k * Vh + s] = make_float4(a.hi, a.lo, c.hi, c.lo);
         }
@@ -181,9 +181,9 @@ __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ canon, cha
                 e_row = fmaxf(e_row, (float)hypot(m[6 + j].x - re, m[6 + j].y + im));
             }
         }
-        double w[12];
+        double w[18];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 9; ++k) {
             w[2 * k] = m[k].x;
             w[2 * k + 1] = m[k].y;
         }
