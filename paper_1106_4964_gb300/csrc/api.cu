@@ -221,9 +221,12 @@ int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a,
         A.y[j] = y[j].data;
         A.y_n[j] = y[j].norm;
         A.sy[j] = sy[j];
+        A.fsy[j] = (float)sy[j];
     }
     A.a = a;
     A.b = b;
+    A.fa = (float)a;
+    A.fb = (float)b;
     A.nrhs = in.nrhs;
     A.g5_core = g5_core;
     A.g5_out = g5_out;
@@ -570,6 +573,7 @@ int ov_create(ov_ctx** ctx, const int dims[4], const double bc_phase[4])
         c->bc[mu] = bc_phase[mu];
         c->g.L[mu] = dims[mu];
         c->g.bc[mu] = bc_phase[mu];
+        c->g.fbc[mu] = (float)bc_phase[mu];
     }
     c->g.Lxh = dims[0] / 2;
     c->g.Vh = (int)(V / 2);

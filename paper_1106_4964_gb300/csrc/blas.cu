@@ -221,9 +221,13 @@ __global__ void __launch_bounds__(RB_THREADS) lincomb_kernel(Geom g, LincombArgs
     using Real = creal_t<P>;
     constexpr size_t CH = nchunk_dev<P>() * 16;
     const int r = blockIdx.y;
-    double2 cf[K];
+    Real cre[K], cim[K];  // coefficients in the arithmetic type, converted once per thread
 #pragma unroll
-    for (int j = 0; j < K; ++j) cf[j] = A.dcoef ? A.dcoef[j * A.out.nrhs + r] : A.hcoef[j];
+    for (int j = 0; j < K; ++j) {
+        const double2 cf = A.dcoef ? A.dcoef[j * A.out.nrhs + r] : A.hcoef[j];
+        cre[j] = (Real)cf.x;
+        cim[j] = (Real)cf.y;
+    }
     double nrm = 0.0;
     const int N = 2 * g.Vh;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(RB_THREADS) lincomb_kernel(Geom g, LincombArgs
             Real v[24];
             load_spinor<P, Real>(A.x[j].data + rp * CH * g.Vh, A.x[j].norm ? A.x[j].norm + rp * g.Vh : nullptr, g.Vh,
                                  s, v);
-            const Real cr = (Real)cf[j].x, ci = (Real)cf[j].y;
+            const Real cr = cre[j], ci = cim[j];
             const bool g5 = (A.g5mask >> j) & 1;
 #pragma unroll
             for (int k = 0; k < 12; ++k) {

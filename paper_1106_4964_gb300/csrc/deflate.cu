@@ -97,14 +97,19 @@ __global__ void __launch_bounds__(512) proj_update_kernel(Geom g, FieldDesc eta,
                                                           FieldDesc out2)
 {
     using Real = dreal_t<PS>;
-    extern __shared__ double2 sh_c[];  // [nev][R] coefficients for out1, then [nev][R] for out2
+    // coefficients in the arithmetic type (converted once per block, not once per site):
+    // (re, im) pairs [nev][R] for out1, then [nev][R] for out2
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    Real* sh_c = reinterpret_cast<Real*>(sh_raw);
     const int R = psi.nrhs;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int k = tid; k < nev * R; k += blockDim.x * blockDim.y) {
-        double2 v = c[k];
-        sh_c[k] = v;
-        double s = sg ? sg[k / R] : 0.0;
-        sh_c[nev * R + k] = make_double2(s * v.x, s * v.y);
+        const double2 v = c[k];
+        const double s = sg ? sg[k / R] : 0.0;
+        sh_c[2 * k] = (Real)v.x;
+        sh_c[2 * k + 1] = (Real)v.y;
+        sh_c[2 * (nev * R + k)] = (Real)(s * v.x);
+        sh_c[2 * (nev * R + k) + 1] = (Real)(s * v.y);
     }
     __syncthreads();
     constexpr size_t CV = nchunk_dev<PV>() * 16, CS = nchunk_dev<PS>() * 16;
@@ -121,16 +126,14 @@ __global__ void __launch_bounds__(512) proj_update_kernel(Geom g, FieldDesc eta,
         Real e[24];
         load_spinor<PV, Real>(eta.data + i * eta_rhs + p * CV * g.Vh,
                               eta.norm ? eta.norm + ((size_t)i * 2 + p) * g.Vh : nullptr, g.Vh, s, e);
-        const double2 c1 = sh_c[i * R + r];
-        const Real cr = (Real)c1.x, ci = (Real)c1.y;
+        const Real cr = sh_c[2 * (i * R + r)], ci = sh_c[2 * (i * R + r) + 1];
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             o1[2 * k] += cr * e[2 * k] - ci * e[2 * k + 1];
             o1[2 * k + 1] += cr * e[2 * k + 1] + ci * e[2 * k];
         }
         if (want2) {
-            const double2 c2 = sh_c[nev * R + i * R + r];
-            const Real dr = (Real)c2.x, di = (Real)c2.y;
+            const Real dr = sh_c[2 * (nev * R + i * R + r)], di = sh_c[2 * (nev * R + i * R + r) + 1];
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 o2[2 * k] += dr * e[2 * k] - di * e[2 * k + 1];
@@ -173,7 +176,7 @@ cudaError_t update2(const Geom& g, const FieldDesc& eta, int nev, const double2*
     const int bx = R >= 8 ? 32 : (R >= 4 ? 64 : 128);
     dim3 block(bx, R);
     dim3 grid((2 * g.Vh + bx - 1) / bx);
-    size_t shm = 2 * sizeof(double2) * nev * R;
+    size_t shm = 4 * sizeof(dreal_t<PS>) * nev * R;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(proj_update_kernel<PV, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)shm);

@@ -137,7 +137,7 @@ __device__ __forceinline__ void hop(const DslashArgs& A, const char* in_q, const
     Real h[12];
     project<MU, S, Real>(v, h);
     if (cross) {
-        Real ph = (Real)A.g.bc[MU];
+        const Real ph = coef<Real>(A.g.bc[MU], A.g.fbc[MU]);
 #pragma unroll
         for (int i = 0; i < 12; ++i) h[i] *= ph;
     }
@@ -212,7 +212,7 @@ __device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int 
     {
         Real self[24];
         load_spinor<SP, Real>(A.in + off, A.in_n ? A.in_n + noff : nullptr, g.Vh, s, self);
-        const Real a = (Real)A.a, b = (Real)A.b;
+        const Real a = coef<Real>(A.a, A.fa), b = coef<Real>(A.b, A.fb);
 #pragma unroll
         for (int i = 0; i < 24; ++i) o[i] = a * self[i] + b * acc[i];
     }
@@ -224,7 +224,7 @@ __device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int 
     for (int j = 0; j < NY; ++j) {
         Real w[24];
         load_spinor<SP, Real>(A.y[j] + off, A.y_n[j] ? A.y_n[j] + noff : nullptr, g.Vh, s, w);
-        const Real sj = (Real)A.sy[j];
+        const Real sj = coef<Real>(A.sy[j], A.fsy[j]);
 #pragma unroll
         for (int i = 0; i < 24; ++i) o[i] += sj * w[i];
     }
@@ -405,14 +405,14 @@ __global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
     float acc[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp0, (float)g.bc[0], acc);
-    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, xm0, (float)g.bc[0], acc);
-    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp0, (float)g.bc[1], acc);
-    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, ym0, (float)g.bc[1], acc);
-    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp0, (float)g.bc[2], acc);
-    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, zm0, (float)g.bc[2], acc);
-    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp0, (float)g.bc[3], acc);
-    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, tm0, (float)g.bc[3], acc);
+    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp0, g.fbc[0], acc);
+    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, xm0, g.fbc[0], acc);
+    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp0, g.fbc[1], acc);
+    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, ym0, g.fbc[1], acc);
+    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp0, g.fbc[2], acc);
+    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, zm0, g.fbc[2], acc);
+    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp0, g.fbc[3], acc);
+    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, tm0, g.fbc[3], acc);
     epilogue<SP, NY>(A, r, p, s, acc);
 }
 
@@ -577,7 +577,7 @@ __device__ __forceinline__ void hop_tma(const DslashArgs& A, const uint8_t* sm, 
     float h[12];
     project<MU, S, float>(v, h);
     if (cross) {
-        const float ph = (float)A.g.bc[MU];
+        const float ph = A.g.fbc[MU];
 #pragma unroll
         for (int k = 0; k < 12; ++k) h[k] *= ph;
     }
@@ -754,7 +754,7 @@ __device__ __forceinline__ void hop_multi(const DslashArgs& A, const char* const
     const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
     float u[18];
     load_link<GP, float>(lb, A.g.Vh, ls, u);
-    const float ph = cross ? (float)A.g.bc[MU] : 1.f;
+    const float ph = cross ? A.g.fbc[MU] : 1.f;
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
         if (j < nr) {

@@ -149,8 +149,20 @@ struct Geom {
     int Lxh;    // Lx / 2
     int Vh;     // sites per parity
     double bc[4];
+    float fbc[4];         // the same phases for FP32 arithmetic (no FP64 conversion in the kernels)
     FastDiv fxh, fy, fz;  // division by Lxh, Ly, Lz
 };
+
+// A host double in the kernel's arithmetic type: FP32 kernels read a copy made on the host,
+// so that they issue no FP64 conversion (GB300's FP64 pipe is narrow).
+template <typename Real>
+__device__ __forceinline__ Real coef(double d, float f)
+{
+    if constexpr (std::is_same<Real, float>::value)
+        return f;
+    else
+        return (Real)d;
+}
 
 // A field of nrhs right-hand sides in the internal layout of one precision.
 struct FieldDesc {

@@ -20,6 +20,7 @@ struct DslashArgs {
     const float* y_n[3];
     double a, b;                 // core = a psi(n) + b * sum of hops
     double sy[3];
+    float fa, fb, fsy[3];        // the same coefficients for FP32 arithmetic
     int nrhs;
     int g5_core, g5_out;
     unsigned* err;               // set to 1 when a bounded wait of a staged variant times out
