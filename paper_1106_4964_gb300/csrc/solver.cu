@@ -403,7 +403,9 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
     for (int it = 0; it < 300; ++it) {
         // degree: even (T_K > 0 below the cut) and capped so that T_K(0) stays within what the work
         // precision resolves (1e12 FP64, 1e10 double-float, 1e4 FP32)
-        const double y0 = (bmax + acut) / (bmax - acut);
+        // largest amplification among the vectors still filtered: at the smallest unlocked Ritz value
+        const double lo_th = it == 0 ? 0.0 : std::max(0.0, std::min(theta[nlock], acut));
+        const double y0 = (bmax + acut - 2.0 * lo_th) / (bmax - acut);
         const double limit = W.tmp[0].prec == P_F64 ? 1e12 : (W.tmp[0].prec == P_DF64 ? 1e10 : 1e4);
         const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
         const int Keff = std::max(2, std::min(K, kmax)) & ~1;
@@ -458,35 +460,38 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d/%d, res[nev-1] %.3e\n", chi, it,
                     acut, Keff, nlock, nev, res[nev - 1]);
         if (nlock >= nev) {
-            // Rayleigh-Ritz with R on the nev leading vectors (splits the +-lambda pairs of R^2)
-            std::vector<cd> M((size_t)nev * nev);
-            for (int j = 0; j < nev; ++j) {
+            // Rayleigh-Ritz with R over the whole block (splits the +-lambda pairs of R^2, both of
+            // whose partners are in the block even where the nev-th Ritz pair is a mixture of them),
+            // then the nev smallest |lambda|
+            const int nr = sq ? nb : nev;
+            std::vector<cd> M((size_t)nr * nr);
+            for (int j = 0; j < nr; ++j) {
                 OV_TRY(R(sub(V, j), W.w));
-                OV_TRY(block_dots(c, V, nev, W.w, st));
-                std::vector<double2> hh(nev);
-                OV_TRY(to_host(c, c->dscal, hh.data(), nev * sizeof(double2), st));
-                for (int i = 0; i < nev; ++i) M[(size_t)i * nev + j] = cd(hh[i].x, hh[i].y);
+                OV_TRY(block_dots(c, V, nr, W.w, st));
+                std::vector<double2> hh(nr);
+                OV_TRY(to_host(c, c->dscal, hh.data(), nr * sizeof(double2), st));
+                for (int i = 0; i < nr; ++i) M[(size_t)i * nr + j] = cd(hh[i].x, hh[i].y);
             }
-            for (int i = 0; i < nev; ++i)
-                for (int j = i; j < nev; ++j) {
-                    const cd a = 0.5 * (M[(size_t)i * nev + j] + std::conj(M[(size_t)j * nev + i]));
-                    M[(size_t)i * nev + j] = a;
-                    M[(size_t)j * nev + i] = std::conj(a);
+            for (int i = 0; i < nr; ++i)
+                for (int j = i; j < nr; ++j) {
+                    const cd a = 0.5 * (M[(size_t)i * nr + j] + std::conj(M[(size_t)j * nr + i]));
+                    M[(size_t)i * nr + j] = a;
+                    M[(size_t)j * nr + i] = std::conj(a);
                 }
             std::vector<double> lam;
             std::vector<cd> Sr;
-            herm_eig(nev, M, lam, Sr);
-            std::vector<int> o(nev);
-            for (int i = 0; i < nev; ++i) o[i] = i;
+            herm_eig(nr, M, lam, Sr);
+            std::vector<int> o(nr);
+            for (int i = 0; i < nr; ++i) o[i] = i;
             std::sort(o.begin(), o.end(), [&](int a, int b) { return std::fabs(lam[a]) < std::fabs(lam[b]); });
-            std::vector<cd> So((size_t)nev * nev);
+            std::vector<cd> So((size_t)nr * nev);
             std::vector<double> lo(nev);
             for (int j = 0; j < nev; ++j) {
                 lo[j] = lam[o[j]];
-                for (int i = 0; i < nev; ++i) So[(size_t)i * nev + j] = Sr[(size_t)i * nev + o[j]];
+                for (int i = 0; i < nr; ++i) So[(size_t)i * nev + j] = Sr[(size_t)i * nr + o[j]];
             }
             FieldDesc eta = sub(W.rot, 0, nev);
-            OV_TRY(rotate(c, V, nev, So, nev, nev, eta, W.zero, st));
+            OV_TRY(rotate(c, V, nr, So, nev, nev, eta, W.zero, st));
             maxres = 0;
             for (int j = 0; j < nev; ++j) {
                 OV_TRY(R(sub(eta, j), W.w));
@@ -555,7 +560,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const int ns = which == 0 ? nev : std::min<long long>(nev / 2 + 4, nev);
     if (ns >= dim / 2) return set_err(c, OV_EINVAL, "nev = %d too large for a lattice of dimension %lld", nev, N);
     // block of the filtered subspace iteration, and the unfiltered Lanczos run that sets the first cut
-    const int nb = (int)std::min<long long>(ns + std::max(10, ns / 2), dim / 2);
+    const int nb = (int)std::min<long long>(ns + std::max(16, (3 * ns) / 4), dim / 2);
     const int m0 = (int)std::min<long long>(nb + 40, dim - 1);
     // operator precision: FP64 when the eigen-residual target needs it; an FP32 filter (FP64
     // Gram-Schmidt and Rayleigh-Ritz) when tol >= 1e-7, or as set by ov_set_option("eig_prec")
