@@ -441,9 +441,17 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         OV_TRY(rotate(c, V, nb, S, nb, nb, W.rot, W.zero, st));
         OV_CUDA(c, cudaMemcpyAsync(V.data, W.rot.data, V.rhs_bytes() * nb, cudaMemcpyDeviceToDevice, st));
         theta = th;
+        // the wanted set, extended over A-degenerate partners of the nev-th pair (for A = R^2 the
+        // +-lambda pairs of R; a Rayleigh-Ritz with R needs both partners, and a larger block would
+        // let unconverged directions produce spurious small Ritz values of the indefinite R)
+        int nw = nev;
+        if (sq) {
+            const double edge = theta[nev - 1] * 1.01 + 1e-300;
+            while (nw < nb - 1 && theta[nw] <= edge) ++nw;
+        }
         // residuals of the wanted Ritz pairs beyond the locked ones; lock the leading converged ones
         nlock = 0;
-        for (int j = 0; j < nev; ++j) {
+        for (int j = 0; j < nw; ++j) {
             if (j == nlock && res[j] <= tolA(theta[j]) * 0.5) {
                 ++nlock;  // was converged before this rotation by a margin: keep it locked
                 continue;
@@ -458,12 +466,11 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         }
         if (verbose())
             fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d/%d, res[nev-1] %.3e\n", chi, it,
-                    acut, Keff, nlock, nev, res[nev - 1]);
-        if (nlock >= nev) {
-            // Rayleigh-Ritz with R over the whole block (splits the +-lambda pairs of R^2, both of
-            // whose partners are in the block even where the nev-th Ritz pair is a mixture of them),
-            // then the nev smallest |lambda|
-            const int nr = sq ? nb : nev;
+                    acut, Keff, nlock, nw, res[nw - 1]);
+        if (nlock >= nw) {
+            // Rayleigh-Ritz with R over the wanted set (splits the +-lambda pairs of R^2), then the
+            // nev smallest |lambda|
+            const int nr = nw;
             std::vector<cd> M((size_t)nr * nr);
             for (int j = 0; j < nr; ++j) {
                 OV_TRY(R(sub(V, j), W.w));
@@ -510,7 +517,7 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            tscale *= 0.1;  // the A-residual threshold was too loose for the R criterion
+            tscale = std::max(tscale * 0.1, 1e-2);  // the A-residual threshold was too loose for R
             nlock = 0;
             std::fill(res.begin(), res.end(), 1e300);
         }
