@@ -451,11 +451,9 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         }
         // residuals of the wanted Ritz pairs beyond the locked ones; lock the leading converged ones
         nlock = 0;
+        // (recomputed for every wanted vector: the Rayleigh-Ritz step may reorder the block, so a
+        // residual from the previous sweep can belong to another vector)
         for (int j = 0; j < nw; ++j) {
-            if (j == nlock && res[j] <= tolA(theta[j]) * 0.5) {
-                ++nlock;  // was converged before this rotation by a margin: keep it locked
-                continue;
-            }
             OV_TRY(Ac(sub(V, j), W.w));
             FieldDesc xs[2] = {W.w, sub(V, j)};
             const double2 h2[2] = {make_double2(1, 0), make_double2(-theta[j], 0)};
@@ -517,7 +515,7 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            tscale = std::max(tscale * 0.1, 1e-2);  // the A-residual threshold was too loose for R
+            tscale = std::max(tscale * 0.3, 0.1);  // the A-residual threshold was too loose for R
             nlock = 0;
             std::fill(res.begin(), res.end(), 1e300);
         }
