@@ -611,7 +611,7 @@ __device__ __forceinline__ void prefetch_link(const DslashArgs& A, int lpar, int
 template <int SP, int GP, int NY, bool PRE>
 __global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashArgs A)
 {
-    extern __shared__ __align__(128) uint8_t sm[];
+    extern __shared__ __align__(16) uint8_t sm[];  // bulk copies need 16-byte alignment
     constexpr int SCH = nchunk_dev<SP>();
     constexpr bool NRM = SP == P_F16 || SP == P_BF16;
     const Geom& g = A.g;

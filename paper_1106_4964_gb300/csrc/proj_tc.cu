@@ -270,7 +270,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     if (!fn) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
     }
