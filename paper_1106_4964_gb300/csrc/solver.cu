@@ -441,19 +441,12 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         OV_TRY(rotate(c, V, nb, S, nb, nb, W.rot, W.zero, st));
         OV_CUDA(c, cudaMemcpyAsync(V.data, W.rot.data, V.rhs_bytes() * nb, cudaMemcpyDeviceToDevice, st));
         theta = th;
-        // the wanted set, extended over A-degenerate partners of the nev-th pair (for A = R^2 the
-        // +-lambda pairs of R; a Rayleigh-Ritz with R needs both partners, and a larger block would
-        // let unconverged directions produce spurious small Ritz values of the indefinite R)
-        int nw = nev;
-        if (sq) {
-            const double edge = theta[nev - 1] * 1.01 + 1e-300;
-            while (nw < nb - 1 && theta[nw] <= edge) ++nw;
-        }
-        // residuals of the wanted Ritz pairs beyond the locked ones; lock the leading converged ones
+        // Lock the leading Ritz vectors whose A-residual is small enough: residuals are recomputed
+        // every sweep (the Rayleigh-Ritz step may reorder the block) and as far as the locked run
+        // extends, past nev when it can (a few block vectors stay unlocked as a buffer).
         nlock = 0;
-        // (recomputed for every wanted vector: the Rayleigh-Ritz step may reorder the block, so a
-        // residual from the previous sweep can belong to another vector)
-        for (int j = 0; j < nw; ++j) {
+        const int jmax = std::max(nev, nb - 4);
+        for (int j = 0; j < jmax; ++j) {
             OV_TRY(Ac(sub(V, j), W.w));
             FieldDesc xs[2] = {W.w, sub(V, j)};
             const double2 h2[2] = {make_double2(1, 0), make_double2(-theta[j], 0)};
@@ -461,14 +454,18 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             res[j] = host_norm(c, W.w, st, &status);
             OV_TRY(status);
             if (j == nlock && res[j] <= tolA(theta[j])) ++nlock;
+            if (j >= nev - 1 && j >= nlock) break;  // the locked run ended
         }
         if (verbose())
-            fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d/%d, res[nev-1] %.3e\n", chi, it,
-                    acut, Keff, nlock, nw, res[nw - 1]);
-        if (nlock >= nw) {
-            // Rayleigh-Ritz with R over the wanted set (splits the +-lambda pairs of R^2), then the
-            // nev smallest |lambda|
-            const int nr = nw;
+            fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d (want %d), res[nev-1] %.3e\n", chi,
+                    it, acut, Keff, nlock, nev, res[nev - 1]);
+        if (nlock >= nev) {
+            // Rayleigh-Ritz with R over every locked vector.  The locked set holds all A-eigenvectors
+            // below its largest Ritz value, so it is R-invariant except where a +-lambda pair of
+            // R^2 = A straddles its edge (a mixture of the two partners); such Ritz pairs show a large
+            // R-residual.  The accepted set is the smallest-|lambda| prefix of good pairs, so that no
+            // mode below the largest accepted |lambda| is left out of the deflation.
+            const int nr = nlock;
             std::vector<cd> M((size_t)nr * nr);
             for (int j = 0; j < nr; ++j) {
                 OV_TRY(R(sub(V, j), W.w));
@@ -489,35 +486,38 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             std::vector<int> o(nr);
             for (int i = 0; i < nr; ++i) o[i] = i;
             std::sort(o.begin(), o.end(), [&](int a, int b) { return std::fabs(lam[a]) < std::fabs(lam[b]); });
-            std::vector<cd> So((size_t)nr * nev);
-            std::vector<double> lo(nev);
-            for (int j = 0; j < nev; ++j) {
+            std::vector<cd> So((size_t)nr * nr);
+            std::vector<double> lo(nr);
+            for (int j = 0; j < nr; ++j) {
                 lo[j] = lam[o[j]];
-                for (int i = 0; i < nr; ++i) So[(size_t)i * nev + j] = Sr[(size_t)i * nr + o[j]];
+                for (int i = 0; i < nr; ++i) So[(size_t)i * nr + j] = Sr[(size_t)i * nr + o[j]];
             }
-            FieldDesc eta = sub(W.rot, 0, nev);
-            OV_TRY(rotate(c, V, nr, So, nev, nev, eta, W.zero, st));
+            FieldDesc eta = sub(W.rot, 0, nr);
+            OV_TRY(rotate(c, V, nr, So, nr, nr, eta, W.zero, st));
+            int good = 0;
             maxres = 0;
-            for (int j = 0; j < nev; ++j) {
+            for (int j = 0; j < nr; ++j) {
                 OV_TRY(R(sub(eta, j), W.w));
                 FieldDesc xs[2] = {W.w, sub(eta, j)};
                 const double2 h2[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
                 OV_TRY(lincomb(c, W.w, 2, xs, h2, nullptr, 0, nullptr, st));
-                const double r = host_norm(c, W.w, st, &status);
+                const double r = host_norm(c, W.w, st, &status) / rscale;
                 OV_TRY(status);
-                maxres = std::max(maxres, r / rscale);
+                if (r > tol) break;
+                maxres = std::max(maxres, r);
+                ++good;
             }
-            if (verbose()) fprintf(stderr, "[ov] chfsi chi=%d: Rayleigh-Ritz max eigen-residual %.3e\n", chi, maxres);
-            if (maxres <= tol) {
+            if (verbose())
+                fprintf(stderr, "[ov] chfsi chi=%d: Rayleigh-Ritz over %d locked vectors, %d good (want %d)\n", chi, nr,
+                        good, nev);
+            if (good >= nev) {
                 OV_CUDA(c, cudaMemcpyAsync(out.data, eta.data, eta.rhs_bytes() * nev, cudaMemcpyDeviceToDevice, st));
                 OV_CUDA(c, cudaStreamSynchronize(st));
-                vals = lo;
+                vals.assign(lo.begin(), lo.begin() + nev);
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            tscale = std::max(tscale * 0.3, 0.1);  // the A-residual threshold was too loose for R
-            nlock = 0;
-            std::fill(res.begin(), res.end(), 1e300);
+            if (nlock >= jmax) tscale = std::max(tscale * 0.3, 0.1);  // nothing left to lock: tighten
         }
         if (theta[nb - 1] > theta[nev - 1] && theta[nb - 1] < acut) acut = theta[nb - 1];
     }
