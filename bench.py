@@ -48,6 +48,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from the ncu capture
+# summarised in profiles/dslash_f32_24c64.md, per (kernel, lattice); None for any other kernel.
+NCU_TRAFFIC = {("dslash_kernel<f32,f32,variant=1>", (24, 24, 24, 64)): 327_243_776}
+
+
 def kernel_name(prec: str, var: int) -> str:
     """The CUDA kernel a dslash launch of this precision and launch variant runs."""
     if var == 3:
@@ -270,7 +275,8 @@ def run_gpu(args):
                    "launch_shape": [bx, by], "variant": var, "launches_per_step": reps},
         "gflops": round(gflops * world, 1),
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(gbs / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(gbs / hbm, 4),
+                     "traffic": NCU_TRAFFIC.get((kernel_name("f32", var), tuple(DIMS))), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": int(bytes_launch),
                      "kernel": kernel_name("f32", var)},
         "variants": variants,
