@@ -319,11 +319,13 @@ struct LanczosWork {
 // (Courant-Fischer), so the filter sharpens as the block converges.  Leading Ritz vectors whose
 // A-residual is small enough are locked (no longer filtered).  Finally the nev leading vectors
 // are rotated by Rayleigh-Ritz with R and accepted when max_i |R eta_i - lam_i eta_i| <=
-// tol * rscale.  sq: A = R^2 (an R-residual e shows as about 2 |lam| e in A).  Vectors go to
-// `out` (nev fields), values (sorted by |lam|) to vals.
+// tol * rscale.  sq: A = R^2 (an R-residual e shows as about 2 |lam| e in A).  refine(): switch
+// A and Awork to the accurate precision (false when they already are); called when the final
+// check fails.  Vectors go to `out` (nev fields), values (sorted by |lam|) to vals.
 int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, double bmax, int nev, int nb,
           double tol, double rscale, bool sq, int chi, unsigned long long seed, LanczosWork& W,
-          std::vector<double>& vals, const FieldDesc& out, double* maxres_out, cudaStream_t st)
+          const std::function<bool()>& refine, std::vector<double>& vals, const FieldDesc& out, double* maxres_out,
+          cudaStream_t st)
 {
     int status = OV_OK;
     const FieldDesc& V = W.basis;
@@ -517,7 +519,13 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 *maxres_out = maxres;
                 return OV_OK;
             }
-            if (nlock >= jmax) tscale = std::max(tscale * 0.3, 0.1);  // nothing left to lock: tighten
+            if (refine()) {
+                // the work precision's own eigenvectors differ from the accurate ones by its rounding
+                // over the gaps; in a dense cluster that mixes many of them: continue accurately
+                if (verbose()) fprintf(stderr, "[ov] chfsi chi=%d: continuing with the accurate operator\n", chi);
+            } else if (nlock >= jmax) {
+                tscale = std::max(tscale * 0.3, 0.1);  // nothing left to lock: tighten
+            }
         }
         if (theta[nb - 1] > theta[nev - 1] && theta[nb - 1] < acut) acut = theta[nb - 1];
     }
@@ -572,7 +580,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : c->hi_prec);
 
     LanczosWork W{};
-    FieldDesc outv{}, tsa{}, tsb{}, ta{};
+    FieldDesc outv{}, ta{};
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);
         field_free(c, &W.basis);
@@ -593,38 +601,50 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &W.zero));
     DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &W.w));
     DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
-    // filter temporaries in the operator's precision: slots of their own (the Clenshaw
-    // buffers are used inside D^dag D)
-    DF_TRY(ws_field(c, WS_LZ_F0, oprec, 1, &W.tmp[0]));
-    DF_TRY(ws_field(c, WS_LZ_F1, oprec, 1, &W.tmp[1]));
-    DF_TRY(ws_field(c, WS_LZ_F2, oprec, 1, &W.tmp[2]));
-    DF_TRY(ws_field(c, WS_LZ_F3, oprec, 1, &W.tmp[3]));
-    if (oprec != P_F64) {
-        DF_TRY(ws_field(c, WS_CG_RS, oprec, 1, &tsa));
-        DF_TRY(ws_field(c, WS_CG_QS, oprec, 1, &tsb));
-    }
     OV_CUDA(c, cudaMemsetAsync(W.zero.data, 0, W.zero.rhs_bytes() * 16, st));
+    // Operator precision `cur`: the filter temporaries (slots of their own: the Clenshaw buffers
+    // are used inside D^dag D) and, below FP64, conversion fields (in, out, middle).
+    int cur = oprec;
+    FieldDesc cva[NPREC] = {}, cvb[NPREC] = {}, cvc[NPREC] = {};
+    auto prepare = [&](int p) -> int {
+        OV_TRY(ws_field(c, WS_LZ_F0, p, 1, &W.tmp[0]));
+        OV_TRY(ws_field(c, WS_LZ_F1, p, 1, &W.tmp[1]));
+        OV_TRY(ws_field(c, WS_LZ_F2, p, 1, &W.tmp[2]));
+        OV_TRY(ws_field(c, WS_LZ_F3, p, 1, &W.tmp[3]));
+        if (p != P_F64) {
+            OV_TRY(ws_field(c, WS_CG_RS, p, 1, &cva[p]));
+            OV_TRY(ws_field(c, WS_CG_QS, p, 1, &cvb[p]));
+            OV_TRY(ws_field(c, WS_LZ_T, p, 1, &cvc[p]));
+        }
+        return OV_OK;
+    };
+    DF_TRY(prepare(oprec));
+    // continue in the accurate precision when the work precision's eigenvectors are not good enough
+    std::function<bool()> refine = [&]() -> bool {
+        const int hi = c->hi_prec;
+        if (cur == hi || cur == P_F64 || prepare(hi) != OV_OK) return false;
+        cur = hi;
+        return true;
+    };
 
     OpFn A, Awork, R;
     double bmax, rscale;
     int K;
-    FieldDesc tsc{};
-    if (oprec != P_F64) DF_TRY(ws_field(c, WS_LZ_T, oprec, 1, &tsc));
     if (which == 0) {
         Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            const FieldDesc& tmid = oprec == P_F64 ? ta : tsc;
+            const FieldDesc& tmid = cur == P_F64 ? ta : cvc[cur];
             OV_TRY(dslash_apply(c, in, tmid, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
             return dslash_apply(c, tmid, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
         };
         A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            if (oprec == P_F64) {
+            if (cur == P_F64) {
                 OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
                 return dslash_apply(c, ta, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
             }
-            OV_TRY(convert(c, in, tsa, st));
-            OV_TRY(dslash_apply(c, tsa, tsc, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-            OV_TRY(dslash_apply(c, tsc, tsb, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-            return convert(c, tsb, out, st);
+            OV_TRY(convert(c, in, cva[cur], st));
+            OV_TRY(dslash_apply(c, cva[cur], cvc[cur], 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            OV_TRY(dslash_apply(c, cvc[cur], cvb[cur], 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return convert(c, cvb[cur], out, st);
         };
         R = [&](const FieldDesc& in, const FieldDesc& out) -> int {
             return dslash_apply(c, in, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
@@ -644,10 +664,10 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
             return c->chiral ? chiral_apply(c, in, out, 0.0, dchi, st) : normal_apply(c, in, out, 0.0, st);
         };
         A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            if (oprec == P_F64) return Awork(in, out);
-            OV_TRY(convert(c, in, tsa, st));
-            OV_TRY(Awork(tsa, tsb));
-            return convert(c, tsb, out, st);
+            if (cur == P_F64) return Awork(in, out);
+            OV_TRY(convert(c, in, cva[cur], st));
+            OV_TRY(Awork(cva[cur], cvb[cur]));
+            return convert(c, cvb[cur], out, st);
         };
         R = A;
         bmax = 4.0 * c->rho * c->rho * 1.01;
@@ -658,14 +678,16 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     double worst = 0;
     for (int s = 0; s < nsec; ++s) {
         const int chi = which == 0 ? 0 : (s == 0 ? +1 : -1);
+        cur = oprec;  // every sector starts in the work precision
+        DF_TRY(prepare(oprec));
         if (which == 1 && c->chiral) {
             const double2 hc[3] = {make_double2(0, 0), make_double2(c->rho, 0), make_double2(chi * c->rho, 0)};
             DF_TRY(to_dev(c, hc, c->dscal + DSCAL_CHCO, sizeof hc, st));
         }
         std::vector<double> v;
         double mr = 0;
-        DF_TRY(chfsi(c, A, Awork, R, K, bmax, ns, nb, tol, rscale, which == 0, chi, 4242ull + 17 * which + s, W, v,
-                     sub(outv, s * ns, ns), &mr, st));
+        DF_TRY(chfsi(c, A, Awork, R, K, bmax, ns, nb, tol, rscale, which == 0, chi, 4242ull + 17 * which + s, W,
+                     refine, v, sub(outv, s * ns, ns), &mr, st));
         allv.insert(allv.end(), v.begin(), v.end());
         worst = std::max(worst, mr);
     }
