@@ -235,6 +235,7 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *   "eig_prec" (-1):  operator precision inside ov_deflate: -1 picks the
  *                    "hi_prec" precision when tol < 1e-5 and FP32 otherwise
  *                    (Gram-Schmidt and Rayleigh-Ritz stay FP64), or an ov_prec;
+ *                    an FP32 run whose final check fails continues in "hi_prec";
  *   "chiral" (0):     1: ov_cg_solve applies D(m)^dag D(m) on the chiral sector
  *                    of each right-hand side as m^2 + (rho^2 - m^2/4)/rho
  *                    (1 + chi gamma5) D(0), one sign application per iteration
