@@ -523,9 +523,10 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
                 // the work precision's own eigenvectors differ from the accurate ones by its rounding
                 // over the gaps; in a dense cluster that mixes many of them: continue accurately
                 if (verbose()) fprintf(stderr, "[ov] chfsi chi=%d: continuing with the accurate operator\n", chi);
-            } else if (nlock >= jmax) {
-                tscale = std::max(tscale * 0.3, 0.1);  // nothing left to lock: tighten
             }
+            // In a dense cluster an A-residual near the locking threshold still mixes neighbouring
+            // modes by more than the R criterion allows: tighten it (the accurate operator resolves it)
+            tscale = std::max(tscale * 0.1, 1e-6);
         }
         if (theta[nb - 1] > theta[nev - 1] && theta[nb - 1] < acut) acut = theta[nb - 1];
     }
