@@ -685,9 +685,9 @@ def main():
     ap.add_argument("--cg-inner", default="f32", help="inner precisions of the propagator CG, comma separated")
     ap.add_argument("--plain-rhs", type=int, default=1,
                     help="propagator: also solve this many sources with the plain FP64 method (0: skip)")
-    ap.add_argument("--chiral", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--chiral", type=int, default=1, choices=[0, 1],
                     help="propagator CG and D^dag D deflation on chiral sectors (one sign per application)")
-    ap.add_argument("--hi-prec", default="f64", choices=["f64", "df64"],
+    ap.add_argument("--hi-prec", default="df64", choices=["f64", "df64"],
                     help="accurate arithmetic of the propagator CG (true residuals): FP64 or double-float")
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--reps", type=int, default=3)
