@@ -144,6 +144,14 @@ def time_dslash(ctx, U_dev, psi_dev, prec, nrhs, steps, warmup, torch):
     return ms
 
 
+def dslash_config(world: int = 1) -> dict:
+    """The headline workload, the same for the GPU arm and the oracle (reference) arm."""
+    return {"workload": "wilson dslash D_w, 24^3x64 even/odd, reconstruct-12, f32, 1 rhs, both parities "
+                        "per launch", "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps",
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2: gauge 170 MB + spinors 2 x 85 MB per launch"}
+
+
 def replica_time(ms: float, dist, device: str) -> float:
     """The job's time per step under replicas: the maximum over ranks (the slowest replica)."""
     if dist is None:
@@ -268,11 +276,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "wilson dslash D_w, 24^3x64 even/odd, reconstruct-12, f32, 1 rhs, both parities "
-                               "per launch", "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: gauge 170 MB + spinors 2 x 85 MB per launch",
-                   "launch_shape": [bx, by], "variant": var, "launches_per_step": reps},
+        "config": dict(dslash_config(world), launch_shape=[bx, by], variant=var, launches_per_step=reps),
         "gflops": round(gflops * world, 1),
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4),
@@ -378,7 +382,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "wilson dslash D_w, 24^3x64, FP64 CPU oracle", "lattice": list(DIMS)},
+        "config": dict(dslash_config(), oracle="the FP64 CPU oracle applies the same D_w (canonical layout)"),
         "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gflops": round(FLOP_SITE * V / dt / 1e9, 3)}))
