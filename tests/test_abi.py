@@ -72,3 +72,16 @@ def test_fast_division_host_side(tmp_path):
                            os.path.join(ROOT, "tests", "fastdiv_check.cu"), "-o", exe])
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
+
+
+def test_binding_enums_match_header():
+    """The status and precision codes of the Python binding are the header's."""
+    import re
+
+    text = open(os.path.join(ROOT, "include", "overlap.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(OV_[A-Z0-9]+)\s*=\s*(-?\d+)", text)}
+    for value, name in binding.STATUS.items():
+        assert codes[name] == value
+    for name in ("OV_F64", "OV_F32", "OV_F16S", "OV_BF16S", "OV_DF64"):
+        assert getattr(binding, name) == codes[name]
+    assert set(binding.PREC.values()) == {codes[n] for n in ("OV_F64", "OV_F32", "OV_F16S", "OV_BF16S", "OV_DF64")}
