@@ -130,6 +130,7 @@ def test_full_size_sampled_sites(big, prec):
     dims, U, psi = big
     ctx = Context(dims, ABC)
     ctx.set_gauge(dev(U))
+    ctx.tune_dslash(prec, 1)  # the launch shape bench.py times
     fi, fo = ctx.field(1, prec), ctx.field(1, prec)
     fi.load(dev(psi))
     ctx.dslash_field(fi, fo, -RHO)
