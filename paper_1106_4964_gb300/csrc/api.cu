@@ -510,10 +510,10 @@ int chiral_setup(ov_ctx* c, const FieldDesc& f, const FieldDesc& tmp, double mas
     const double cm = (c->rho * c->rho - 0.25 * mass * mass) / c->rho;
     std::vector<double2> hc(5 * R);
     for (int q = 0; q < R; ++q) {
-        const double n2 = hn[q].x;
-        if (!(n2 > 0) || !(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
+        const double n2 = hn[q].x;  // a zero right-hand side lies in both sectors
+        if (!(n2 >= 0) || !(std::fabs(std::fabs(hg[q].x) - n2) <= 1e-12 * n2))
             return set_err(c, OV_EINVAL, "chiral mode needs right-hand sides of definite chirality (rhs %d)", q);
-        const double chi = hg[q].x > 0 ? 1.0 : -1.0;
+        const double chi = hg[q].x >= 0 ? 1.0 : -1.0;
         hc[q] = make_double2(mass * mass, 0);
         hc[R + q] = make_double2(cm, 0);
         hc[2 * R + q] = make_double2(chi * cm, 0);
