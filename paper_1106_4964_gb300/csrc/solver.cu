@@ -4,8 +4,9 @@
 //    filtered by T_K(Y(A)) of A = H_w^2 (Sec. V: Chebyshev acceleration, eigenvectors of T_n(H_w^2))
 //    or of A = D^dag D, Rayleigh-Ritz with A every sweep, the filter's cut following the block's Ritz
 //    values, then Rayleigh-Ritz with H_w for the signed eigenvalues of Eq. 7;
-//  * cg_impl: deflated CG on D(m)^dag D(m) (Eq. 9) with mixed precision and FP64 reliable updates,
-//    optionally preconditioned by the learned network (flexible CG, net.cu).
+//  * cg_impl: deflated CG on D(m)^dag D(m) (Eq. 9) with mixed precision and reliable updates in FP64
+//    or double-float, optionally with the one-sign chiral-sector inner operator (chiral_apply, api.cu)
+//    and preconditioned by the learned network (flexible CG, net.cu).
 // The paper uses implicitly restarted Arnoldi on the filtered operator; the operators here are
 // Hermitian, and a filtered block iteration lets the filter interval adapt between sweeps.
 #include <algorithm>
