@@ -229,6 +229,27 @@ def cg(dims, bc, U, rho, mass, lmax, eps, coeffs, b, tol=1e-10, max_iter=1000, e
     return x, it, res.value
 
 
+def multimass_cg(dims, bc, U, rho, lmax, eps, coeffs, b, masses, tol=1e-10, max_iter=1000, evals=None,
+                 evecs=None, mu=None, xi=None):
+    """One multi-shifted CG for D(m)^dag D(m) x_m = b at every mass m (Sec. II), the low modes
+    (mu, xi) of the massless D^dag D deflated.  Returns (x [nmass, V, 4, 3], iterations,
+    true relative residuals per mass with the two-sign operator)."""
+    V = volume(dims)
+    b = _field(b, V)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    masses = np.ascontiguousarray(masses, dtype=np.float64)
+    nev, lam, eta = _defl(evals, evecs, V)
+    nev2, mu_, xi_ = _defl(mu, xi, V)
+    x = np.empty((len(masses),) + b.shape, dtype=np.complex128)
+    res = np.empty(len(masses))
+    it = lib().or_multimass_cg(_dims(dims), _bc(bc), _ptr(_gauge(U, V)), ctypes.c_double(rho),
+                               ctypes.c_double(lmax), ctypes.c_double(eps), ctypes.c_int(len(coeffs) - 1),
+                               _ptr(coeffs), ctypes.c_int(nev), _ptr(lam), _ptr(eta), ctypes.c_int(nev2), _ptr(mu_),
+                               _ptr(xi_), ctypes.c_int(len(masses)), _ptr(masses), _ptr(b), _ptr(x),
+                               ctypes.c_double(tol), ctypes.c_int(max_iter), _ptr(res))
+    return x, it, res
+
+
 def net_layer(dims, bc, U, W, x):
     """One gauge-covariant layer: W [9, cout, cin, 4, 4], x [cin, V, 4, 3] -> y [cout, V, 4, 3]."""
     V = volume(dims)

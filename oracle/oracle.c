@@ -525,6 +525,128 @@ int or_cg(const int *d, const double *bc, const cplx *U, double rho, double mass
 }
 
 /* ------------------------------------------------------------------ */
+/* multi-mass CG (Sec. II: one multi-shifted CG for several quark       */
+/* masses, with the low modes of the massless D^dag D deflated)          */
+/* ------------------------------------------------------------------ */
+/* With sign^2 = 1, D(m)^dag D(m) = a_m (D^dag D + s_m), a_m = 1 - m^2/(4 rho^2),
+ * s_m = m^2 / a_m (D = D(0) from Eq. 8; D^dag D = rho (D + D^dag)).  All masses
+ * therefore share the Krylov space of D^dag D: the shifted systems
+ * (D^dag D + s_k) y_k = b_h are solved by one CG recursion on D^dag D whose
+ * shifted residuals are collinear with the base residual, r_k = z_k r, and
+ * x_k = y_k / a_k + sum_i xi_i (xi_i^dag b) / (a_k mu_i + m_k^2) (Eq. 9).
+ * The coefficient recurrences (z_k, alpha_k, beta_k) are those of the
+ * shifted-system CG of Jegerlehner (1996), with base shift 0:
+ *   z_k' = z_k z_k^- alpha^- / (alpha beta^- (z_k^- - z_k) + z_k^- alpha^- (1 + s_k alpha)),
+ *   alpha_k = alpha z_k' / z_k,  beta_k = beta (z_k' / z_k)^2,  p_k <- z_k' r + beta_k p_k.
+ * Each mass stops updating once |z_k| |r| <= tol |b_h|.  true_res[k] is the
+ * relative residual of x_k with the full two-sign D(m_k)^dag D(m_k).
+ * Returns the number of iterations. */
+int or_multimass_cg(const int *d, const double *bc, const cplx *U, double rho, double lmax, double eps, int n,
+                    const double *c, int nev, const double *lam, const cplx *eta, int nev2, const double *mu,
+                    const cplx *xi, int nm, const double *masses, const cplx *b, cplx *x, double tol,
+                    int max_iter, double *true_res)
+{
+    init_gamma();
+    long N = 12 * volume(d);
+    sign_args a = {d, bc, U, -rho, lmax, eps, n, c, nev, lam, eta};
+    cplx *r = malloc(sizeof(cplx) * N), *p = malloc(sizeof(cplx) * N);
+    cplx *q = malloc(sizeof(cplx) * N), *t = malloc(sizeof(cplx) * N);
+    cplx *pk = malloc(sizeof(cplx) * N * nm);
+    double *am = malloc(sizeof(double) * nm), *sm = malloc(sizeof(double) * nm);
+    double *z = malloc(sizeof(double) * nm), *zo = malloc(sizeof(double) * nm);
+    double *zn = malloc(sizeof(double) * nm);
+    int *active = malloc(sizeof(int) * nm);
+    for (int k = 0; k < nm; ++k) {
+        am[k] = 1.0 - masses[k] * masses[k] / (4.0 * rho * rho);
+        sm[k] = masses[k] * masses[k] / am[k];
+        z[k] = zo[k] = 1.0;
+        active[k] = 1;
+    }
+    /* b_h = b - sum_i xi_i (xi_i^dag b); low-mode coefficients kept for the end */
+    memcpy(r, b, sizeof(cplx) * N);
+    cplx *pb = malloc(sizeof(cplx) * (nev2 > 0 ? nev2 : 1));
+    for (int i = 0; i < nev2; ++i) {
+        const cplx *e = xi + (long)i * N;
+        pb[i] = vdot(N, e, b);
+        for (long k = 0; k < N; ++k) r[k] -= pb[i] * e[k];
+    }
+    double bh = sqrt(vnorm2(N, r));
+    memset(x, 0, sizeof(cplx) * N * nm);
+    memcpy(p, r, sizeof(cplx) * N);
+    for (int k = 0; k < nm; ++k) memcpy(pk + (long)k * N, r, sizeof(cplx) * N);
+    double rr = vnorm2(N, r), alpha_o = 1.0, beta_o = 0.0;
+    int iters = 0;
+    while (iters < max_iter && bh > 0) {
+        int any = 0;
+        for (int k = 0; k < nm; ++k) any |= active[k];
+        if (!any) break;
+        ddag_d(&a, rho, 0.0, p, q, t); /* massless D^dag D on the deflated complement */
+        for (int i = 0; i < nev2; ++i) {
+            const cplx *e = xi + (long)i * N;
+            cplx pr = vdot(N, e, q);
+            for (long k = 0; k < N; ++k) q[k] -= pr * e[k];
+        }
+        double alpha = rr / creal(vdot(N, p, q));
+        for (int k = 0; k < nm; ++k) {
+            zn[k] = z[k];
+            if (!active[k]) continue;  /* a finished mass keeps its solution */
+            zn[k] = z[k] * zo[k] * alpha_o /
+                    (alpha * beta_o * (zo[k] - z[k]) + zo[k] * alpha_o * (1.0 + sm[k] * alpha));
+            double ak = alpha * zn[k] / z[k];
+            cplx *xk = x + (long)k * N, *p_k = pk + (long)k * N;
+            for (long j = 0; j < N; ++j) xk[j] += ak * p_k[j];
+        }
+        for (long j = 0; j < N; ++j) r[j] -= alpha * q[j];
+        double rr_new = vnorm2(N, r), beta = rr_new / rr;
+        ++iters;
+        for (int k = 0; k < nm; ++k) {
+            if (active[k]) {
+                double bk = beta * (zn[k] / z[k]) * (zn[k] / z[k]);
+                cplx *p_k = pk + (long)k * N;
+                for (long j = 0; j < N; ++j) p_k[j] = zn[k] * r[j] + bk * p_k[j];
+                if (fabs(zn[k]) * sqrt(rr_new) <= tol * bh) active[k] = 0;
+            }
+            if (zn[k] != z[k]) {
+                zo[k] = z[k];
+                z[k] = zn[k];
+            }
+        }
+        for (long j = 0; j < N; ++j) p[j] = r[j] + beta * p[j];
+        alpha_o = alpha;
+        beta_o = beta;
+        rr = rr_new;
+    }
+    /* x_k = y_k / a_k + low-mode part; true residuals with the two-sign operator */
+    double bnorm = sqrt(vnorm2(N, b));
+    for (int k = 0; k < nm; ++k) {
+        cplx *xk = x + (long)k * N;
+        for (long j = 0; j < N; ++j) xk[j] /= am[k];
+        for (int i = 0; i < nev2; ++i) {
+            const cplx *e = xi + (long)i * N;
+            double muk = am[k] * mu[i] + masses[k] * masses[k];
+            if (muk > 0)
+                for (long j = 0; j < N; ++j) xk[j] += (pb[i] / muk) * e[j];
+        }
+        ddag_d(&a, rho, masses[k], xk, q, t);
+        for (long j = 0; j < N; ++j) q[j] = b[j] - q[j];
+        true_res[k] = sqrt(vnorm2(N, q)) / bnorm;
+    }
+    free(r);
+    free(p);
+    free(q);
+    free(t);
+    free(pk);
+    free(am);
+    free(sm);
+    free(z);
+    free(zo);
+    free(zn);
+    free(active);
+    free(pb);
+    return iters;
+}
+
+/* ------------------------------------------------------------------ */
 /* gauge-covariant network layer (the learned preconditioner)           */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart; the layer is defined from the parallel
