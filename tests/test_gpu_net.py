@@ -1,6 +1,6 @@
 """GPU parity of the learned gauge-covariant preconditioner against the FP64
 oracle (forward pass and loss gradient, FP32 tolerance), then training on
-the library's own CG pairs and flexible CG judged by the true FP64 residual,
+the library's own CG pairs and flexible CG checked by the true FP64 residual,
 with the gain over plain deflated CG reported."""
 import numpy as np
 import pytest
