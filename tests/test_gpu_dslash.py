@@ -211,3 +211,23 @@ def test_autotuned_shape_parity(prec):
         got = host(out)
         for r in range(nrhs):
             assert rel(got[r], oracle.dslash(dims, ABC, U, 0.2, psi[r])) <= TOL[prec], shape
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("df64", 1e-12), ("f32", 1e-6)])
+def test_full_size_hw_hermiticity(big, prec, tol):
+    """A property that holds at any size, checked on the whole 24^3 x 64 lattice: H_w is
+    Hermitian, <u, H_w v> = <H_w u, v> (gamma5-hermiticity of D_w, Sec. II)."""
+    from paper_1106_4964_gb300 import Context
+
+    dims, U, _ = big
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    u = dev(synth.gaussian_spinor(dims, 41))
+    v = dev(synth.gaussian_spinor(dims, 42))
+    hu, hv = torch.empty_like(u), torch.empty_like(v)
+    ctx.apply_Hw(u, hu, -RHO, prec=prec)
+    ctx.apply_Hw(v, hv, -RHO, prec=prec)
+    lhs = torch.vdot(u.reshape(-1), hv.reshape(-1)).item()
+    rhs = torch.vdot(hu.reshape(-1), v.reshape(-1)).item()
+    scale = (torch.linalg.vector_norm(u) * torch.linalg.vector_norm(hv)).item()
+    assert abs(lhs - rhs) <= tol * scale
