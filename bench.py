@@ -1,17 +1,20 @@
 """Benchmark of the overlap hot path on GB300.
 
-Default workload (the dslash-throughput configuration): Wilson dslash on a
-24^3 x 64 lattice, even/odd layout with both parities in one launch,
-reconstruct-12 links from exp(0.5 i H) + 3 APE steps (alpha 0.6) +
-re-unitarisation, Gaussian spinors, FP32 storage and arithmetic, 1 RHS.
+Default workload (the dslash-throughput configuration at the paper's
+precision): Wilson dslash on a 24^3 x 64 lattice, even/odd layout with both
+parities in one launch, links from exp(0.5 i H) + 3 APE steps (alpha 0.6) +
+re-unitarisation, Gaussian spinors, FP64 storage and arithmetic, 1 RHS.
 One step = one full-lattice D_w application (one kernel launch).
 
-`value` is algorithmic GB/s of that kernel: the compulsory traffic of a full
-D_w in one pass, 96 reals per site (4 reconstruct-12 links, the input
-spinor, the output spinor), divided by the CUDA-event time.  The JSON line
-also carries GFLOP/s (1320 flop/site), the FP64/FP16/BF16 and 12-RHS
-variants, an end-to-end figure through the C ABI with host buffers, the
-oracle timed on the host cores, and the SM clocks sampled while timing.
+`value` is GFLOP/s of that kernel (1320 flop per site, the hopping term)
+divided by the CUDA-event time.  On GB300 the FP64 dslash is bound by the
+FP64 pipe, so its roofline is the FMA throughput measured in the same run by
+the library's own FMA kernel.  The JSON line also carries algorithmic GB/s,
+the FP32 / FP16 / BF16 / double-float and 12-RHS variants (the FP32 one with
+its HBM roofline), a small propagator solve (12 point sources to the FP64
+true residual 1e-10), an end-to-end figure through the C ABI with host
+buffers, the oracle timed on the host cores, and the SM clocks sampled while
+timing.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): replicas only, each rank runs the same workload on its own GPU.
@@ -19,6 +22,7 @@ Multi-GPU (torchrun): replicas only, each rank runs the same workload on its own
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -37,6 +41,8 @@ RHO = 1.5
 METRIC = "dslash GB/s & GFLOP/s (% HBM roofline); overlap propagator solves/s at res 1e-10"
 REAL_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "df64": 8}
 FLOP_SITE = 1320
+HEADLINE_PREC = "f64"
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 
 
 def peaks():
@@ -48,23 +54,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from the ncu capture
-# summarised in profiles/dslash_f32_24c64.md, per (kernel, lattice); None for any other kernel.
-NCU_TRAFFIC = {("dslash_kernel<f32,f32,variant=1>", (24, 24, 24, 64)): 327_243_776}
+def kernel_sources_sha() -> str:
+    """Hash of the dslash kernel's sources: a DRAM-traffic figure from an ncu capture holds only
+    while the kernel it was taken on is unchanged."""
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "ov_internal.cuh", "ov_kernels.h"):
+        with open(os.path.join(ROOT, "paper_1106_4964_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def kernel_name(prec: str, var: int) -> str:
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu captures
+# summarised under profiles/, keyed by (kernel, lattice, sources hash at capture time).  A kernel whose
+# sources changed since its capture gets null.
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(kernel: str):
+    return NCU_TRAFFIC.get((kernel, tuple(DIMS), kernel_sources_sha()))
+
+
+def kernel_name(prec: str, var: int, nrhs: int = 1) -> str:
     """The CUDA kernel a dslash launch of this precision and launch variant runs."""
     if var == 3:
         return f"dslash_staged_kernel<{prec},{prec}>"
     if var in (4, 5):
         return f"dslash_tma_kernel<{prec},{prec},links_prefetched={var == 5}>"
+    if var in (6, 7):
+        return f"dslash_multi_kernel<{prec},{prec},rhs_per_thread={2 if var == 6 else 4}>"
     return f"dslash_kernel<{prec},{prec},variant={var}>"
 
 
 def site_bytes(prec: str, nrhs: int = 1) -> float:
-    """Compulsory bytes per site and RHS of a one-pass full D_w: links 48 reals shared by
-    the RHS, input and output spinors 24 reals each (16-bit spinors add a 4-byte scale)."""
+    """Compulsory bytes per site and RHS of a one-pass full D_w: 4 reconstruct-12 links (48 reals)
+    shared by the RHS, input and output spinors 24 reals each (16-bit spinors add a 4-byte
+    scale).  The FP64 and double-float kernels store all 18 reals of a link (they are bound by
+    arithmetic, not bandwidth); the algorithmic figure keeps the 12-real minimum."""
     rb = REAL_BYTES[prec]
     spin = 24 * rb + (4 if prec in ("f16", "bf16") else 0)
     return 48 * rb / nrhs + 2 * spin
@@ -123,11 +148,12 @@ def make_inputs(nrhs=1):
     return U, psi
 
 
-def time_dslash(ctx, U_dev, psi_dev, prec, nrhs, steps, warmup, torch):
-    """Average CUDA-event time of one D_w launch (internal fields, current stream)."""
+def time_dslash(ctx, psi_dev, prec, nrhs, steps, warmup, torch):
+    """Average CUDA-event time of one D_w launch (internal fields, current stream) in the
+    autotuned launch shape; returns (ms, (bx, by, variant))."""
     fi, fo = ctx.field(nrhs, prec), ctx.field(nrhs, prec)
     fi.load(psi_dev)
-    ctx.tune_dslash(prec, nrhs)
+    shape = ctx.tune_dslash(prec, nrhs)
     st = torch.cuda.current_stream()
     for _ in range(warmup):
         ctx.dslash_field(fi, fo, -RHO)
@@ -141,15 +167,15 @@ def time_dslash(ctx, U_dev, psi_dev, prec, nrhs, steps, warmup, torch):
     ms = e0.elapsed_time(e1) / steps
     fi.close()
     fo.close()
-    return ms
+    return ms, shape
 
 
 def dslash_config(world: int = 1) -> dict:
     """The headline workload, the same for the GPU arm and the oracle (reference) arm."""
-    return {"workload": "wilson dslash D_w, 24^3x64 even/odd, reconstruct-12, f32, 1 rhs, both parities "
-                        "per launch", "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps",
-            "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2: gauge 170 MB + spinors 2 x 85 MB per launch"}
+    return {"workload": "wilson dslash D_w, 24^3x64 even/odd, FP64 storage and arithmetic (the paper's "
+                        "precision), 1 rhs, both parities per launch", "lattice": list(DIMS),
+            "gauge": "exp(0.5 iH) + 3 APE(0.6) steps", "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2: gauge 510 MB + spinors 2 x 170 MB per launch"}
 
 
 def replica_time(ms: float, dist, device: str) -> float:
@@ -189,9 +215,13 @@ def run_gpu(args):
     ctx.set_gauge(U_dev)
     psi_dev = torch.from_numpy(psi).cuda()
     hbm, peak_kind = peaks()
+    # ALU rooflines: FMA throughput of this GPU, measured by the library's own FMA kernel
+    fma = {"f64_gflops": round(ov.measure_fma_peak("f64"), 1), "f32_gflops": round(ov.measure_fma_peak("f32"), 1),
+           "how": "ov_measure_fma_peak: 8 independent FMA chains per thread, 8 x 256 threads per SM, "
+                  "best of 5 launches (CUDA events), 2 flop per FMA"}
 
-    # ---- headline: f32, 1 rhs (timed region bracketed by barrier + synchronize)
-    prec = "f32"
+    # ---- headline: FP64, 1 rhs (timed region bracketed by barrier + synchronize)
+    prec = HEADLINE_PREC
     fi, fo = ctx.field(1, prec), ctx.field(1, prec)
     fi.load(psi_dev)
     if args.shape:
@@ -211,6 +241,7 @@ def run_gpu(args):
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, int(args.inner))
+    n0 = ctx.dslash_count()
     t_wall = time.perf_counter()
     e0.record(st)
     for _ in range(args.steps * reps):
@@ -218,8 +249,10 @@ def run_gpu(args):
     e1.record(st)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    launches = ctx.dslash_count() - n0
     if dist:
         dist.barrier()
+    time.sleep(0.3)
     clocks = clk.stop()
     ms = replica_time(e0.elapsed_time(e1) / (args.steps * reps), dist, "cuda")
     bytes_launch = V * site_bytes(prec, 1)
@@ -228,22 +261,25 @@ def run_gpu(args):
     fi.close()
     fo.close()
 
-    # ---- variants (same workload, other precisions and 12 rhs)
+    # ---- variants (same lattice, other precisions and 12 rhs); the FP32 one is bound by HBM
     variants = {}
     if not args.quick:
-        for p in ("f64", "df64", "f16", "bf16"):
-            t = time_dslash(ctx, U_dev, psi_dev, p, 1, min(2000, max(5, args.steps)), args.warmup, torch)
+        for p in ("f32", "f16", "bf16", "df64"):
+            t, sh = time_dslash(ctx, psi_dev, p, 1, min(2000, max(20, args.steps)), args.warmup, torch)
             b = V * site_bytes(p, 1)
             variants[f"{p}_r1"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
                                    "GFLOPps": round(FLOP_SITE * V / t / 1e6, 1),
-                                   "frac_hbm": round(b / t / 1e6 / hbm, 3)}
+                                   "frac_hbm": round(b / t / 1e6 / hbm, 3), "kernel": kernel_name(p, sh[2]),
+                                   "shape": list(sh)}
+        variants["df64_r1"]["frac_f32_fma_note"] = "double-float is bound by the FP32 pipe, not HBM"
         psi12 = torch.from_numpy(make_inputs_rhs(12)).cuda()
         for p in ("f32", "f16", "f64", "df64"):
-            t = time_dslash(ctx, U_dev, psi12, p, 12, min(300, max(3, args.steps // 2)), args.warmup, torch)
+            t, sh = time_dslash(ctx, psi12, p, 12, min(300, max(5, args.steps // 2)), args.warmup, torch)
             b = V * 12 * site_bytes(p, 12)
             variants[f"{p}_r12"] = {"ms": round(t, 4), "GBps": round(b / t / 1e6, 1),
                                     "GFLOPps": round(12 * FLOP_SITE * V / t / 1e6, 1),
-                                    "frac_hbm": round(b / t / 1e6 / hbm, 3)}
+                                    "frac_hbm": round(b / t / 1e6 / hbm, 3), "kernel": kernel_name(p, sh[2], 12),
+                                    "shape": list(sh), "ms_per_rhs": round(t / 12, 4)}
         del psi12
 
     # ---- end to end through the C ABI with pinned host buffers (H2D + pack + dslash + unpack + D2H)
@@ -258,15 +294,23 @@ def run_gpu(args):
         ctx.apply_dslash(hin.numpy(), hout.numpy(), -RHO, prec=prec)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ne
-    e2e = {"value": round(bytes_launch / e2e_s / 1e9, 2), "unit": "GB/s",
+    e2e = {"value": round(FLOP_SITE * V / e2e_s / 1e9, 2), "unit": "GFLOP/s",
            "h2d_bytes_per_step": int(hin.numel() * hin.element_size()),
            "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
            "ms_per_step": round(e2e_s * 1e3, 3)}
+    ctx.close()
+    del U_dev, psi_dev
+    torch.cuda.empty_cache()
 
+    prop = None
+    if not args.quick and not args.no_prop and rank == 0:
+        prop = propagator_record(args)
+
+    kern = kernel_name(prec, var)
     out = {
         "metric": METRIC,
-        "value": round(replica_throughput(bytes_launch, world, ms) / 1e9, 2),
-        "unit": "GB/s",
+        "value": round(replica_throughput(FLOP_SITE * V / 1e9, world, ms), 2),
+        "unit": "GFLOP/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -274,28 +318,80 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": prec,
         "data": "synthetic",
         "config": dict(dslash_config(world), launch_shape=[bx, by], variant=var, launches_per_step=reps),
-        "gflops": round(gflops * world, 1),
-        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(gbs / hbm, 4),
-                     "traffic": NCU_TRAFFIC.get((kernel_name("f32", var), tuple(DIMS))), "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": int(bytes_launch),
-                     "kernel": kernel_name("f32", var)},
+        "GBps": round(gbs * world, 1),
+        "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": fma["f64_gflops"], "unit": "GFLOP/s",
+                     "frac": round(gflops / fma["f64_gflops"], 4), "traffic": ncu_traffic(kern),
+                     "peak_kind": "measured: FP64 FMA throughput of this GPU (ov_measure_fma_peak, same run)",
+                     "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_nominal": round(gflops / FP64_NOMINAL_GFLOPS, 4),
+                     "algorithmic_flops_per_launch": FLOP_SITE * V, "kernel": kern,
+                     "hbm": {"achieved": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 4),
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_launch)}},
+        "fma_peaks": fma,
         "variants": variants,
+        "propagator": prop,
         "e2e": e2e,
-        "gpu_launches": args.steps * reps,
+        "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed": round(t_wall, 4),
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(U, psi, args)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def propagator_record(args):
+    """A small propagator at the paper's precision, inside the default run: the 12 spin-colour point
+    sources on an 8^3 x 16 lattice (the same link generator), rho 1.5, the lowest 16 H_w modes deflated
+    in the sign (degree 100 on the rest) and the lowest 16 D^dag D modes deflating the CG, one
+    multi-RHS mixed-precision CG (FP32 inner operator on the chiral sectors, FP64 true residuals and
+    reliable updates) to the FP64 true residual 1e-10.  Set-up (eigensolvers) is timed apart."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+    import synth
+
+    dims = tuple(args.prop_dims)
+    U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
+    ctx = ov.Context(dims, BC)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    ctx.set_option("hi_prec", ov.PREC["f64"])
+    setup = {}
+    t0 = time.perf_counter()
+    ctx.set_sign_poly(RHO, 0.05, 100, 0.0)
+    lmax = ctx.get_sign_poly()["lambda_max"]
+    ctx.deflate(0, args.prop_nev, 1e-8)
+    vals, _ = ctx.get_eigenpairs(0)
+    eps = (0.99 * np.abs(vals).max() / lmax) ** 2
+    ctx.set_sign_poly(RHO, eps, 100, lmax)
+    setup["deflate_hw"] = time.perf_counter() - t0
+    ctx.set_option("chiral", 1)
+    t0 = time.perf_counter()
+    ctx.deflate(1, args.prop_nev, 1e-8)
+    setup["deflate_dd"] = time.perf_counter() - t0
+    ctx.tune_dslash("f32", 12)
+    b = torch.from_numpy(synth.point_sources(dims)).cuda()
+    x = torch.empty_like(b)
+    n0 = ctx.dslash_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = ctx.cg_solve(b, x, mass=args.mass, tol=1e-10, max_iter=3000, inner_prec="f32")
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    rec = {"workload": f"12 point sources, {dims[0]}^3x{dims[3]}, rho 1.5, mass {args.mass}, {args.prop_nev} H_w + "
+                       f"{args.prop_nev} D^dag D modes, degree 100, eps {eps:.4g}",
+           "solves_per_s": round(12 / t, 4), "propagators_per_s": round(1 / t, 5), "seconds": round(t, 3),
+           "iterations": info["iterations"], "reliable_updates": info["reliable_updates"],
+           "max_fp64_true_residual": max(info["true_residual"]), "dslash_launches": ctx.dslash_count() - n0,
+           "graphs": list(ctx.graph_stats()), "setup_s": {k: round(v, 2) for k, v in setup.items()},
+           "method": "FP32 inner operator (one-sign chiral form), FP64 true residuals and reliable updates"}
+    ctx.close()
+    return rec
 
 
 def make_inputs_rhs(nrhs):
@@ -326,13 +422,11 @@ def cpu_baseline(U, psi, args):
     oracle.dslash(DIMS, BC, U, -RHO, psi[0])
     dt1 = time.perf_counter() - t1
     oracle.set_threads(cores)
-    return {"value": round(V * site_bytes("f32", 1) / dt / 1e9, 4), "unit": "GB/s", "cores": cores,
-            "kind": "oracle", "gflops": round(FLOP_SITE * V / dt / 1e9, 3),
-            "one_core": {"value": round(V * site_bytes("f32", 1) / dt1 / 1e9, 4), "unit": "GB/s",
-                         "gflops": round(FLOP_SITE * V / dt1 / 1e9, 3)},
+    return {"value": round(FLOP_SITE * V / dt / 1e9, 3), "unit": "GFLOP/s", "cores": cores,
+            "kind": "oracle", "GBps": round(V * site_bytes("f64", 1) / dt / 1e9, 3),
+            "one_core": {"value": round(FLOP_SITE * V / dt1 / 1e9, 3), "unit": "GFLOP/s"},
             "sample": f"{n} full D_w applications of the 24^3x64 lattice (FP64 oracle), {dt * 1e3:.1f} ms each "
-                      f"on {cores} threads, one more on 1 thread ({dt1 * 1e3:.0f} ms); value in the same "
-                      "algorithmic-bytes unit as the GPU line"}
+                      f"on {cores} threads, one more on 1 thread ({dt1 * 1e3:.0f} ms)"}
 
 
 def cpu_dw_extrapolation(U, dims, launches, args):
@@ -360,7 +454,8 @@ def cpu_dw_extrapolation(U, dims, launches, args):
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only), the same D_w on the
+    same lattice, in the same unit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -376,16 +471,17 @@ def run_reference(args):
         oracle.dslash(DIMS, BC, U, -RHO, psi[0])
     dt = (time.perf_counter() - t0) / args.steps
     cores = oracle.threads()
-    val = round(V * site_bytes("f32", 1) / dt / 1e9, 4)
-    sample = f"{args.steps} full D_w applications of the 24^3x64 lattice (FP64 oracle)"
+    val = round(FLOP_SITE * V / dt / 1e9, 3)
+    sample = (f"{args.steps} full D_w applications of the 24^3x64 lattice by the FP64 CPU oracle (canonical "
+              "layout, plain loops, OpenMP)")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(dslash_config(), oracle="the FP64 CPU oracle applies the same D_w (canonical layout)"),
-        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
-        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "gflops": round(FLOP_SITE * V / dt / 1e9, 3)}))
+        "config": dslash_config(args.gpus),
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "GBps": round(V * site_bytes("f64", 1) / dt / 1e9, 3)}))
 
 
 # ---------------------------------------------------------------------------------------
@@ -435,7 +531,7 @@ def run_overlap(args):
             ctx.tune_dslash(prec, nrhs)
             fi, fo = ctx.field(nrhs, prec), ctx.field(nrhs, prec)
             fi.load(src)
-            ctx.overlap_field(fi, fo)  # graph capture
+            ctx.overlap_field(fi, fo)  # eager run, then capture of the graph that the timed calls replay
             torch.cuda.synchronize()
             n0 = ctx.dslash_count()
             e0, e1 = _events(torch)
@@ -664,6 +760,21 @@ def run_learned(args):
                    "hi_prec": args.hi_prec, "chiral": bool(args.chiral)}, "results": res}))
 
 
+def run_peaks(args):
+    """FMA throughput of this GPU (FP64 and FP32) by the library's own kernel, and the copy
+    bandwidth the driver measured: the denominators of every roofline in the default line."""
+    import torch
+
+    import paper_1106_4964_gb300 as ov
+
+    torch.cuda.set_device(0)
+    hbm, kind = peaks()
+    res = {p: [round(ov.measure_fma_peak(p), 1) for _ in range(3)] for p in ("f64", "f32")}
+    print(json.dumps({"metric": "FMA throughput", "value": max(res["f64"]), "unit": "GFLOP/s", "n_gpus": 1,
+                      "dtype": "f64", "fma_gflops": res, "hbm_gbs": hbm, "hbm_kind": kind,
+                      "nominal": {"f64_gflops": FP64_NOMINAL_GFLOPS}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,10 +784,14 @@ def main():
     ap.add_argument("--inner", type=int, default=1, help="launches per step")
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-prop", action="store_true", help="skip the propagator record of the default run")
+    ap.add_argument("--prop-dims", type=int, nargs=4, default=[8, 8, 8, 16])
+    ap.add_argument("--prop-nev", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("BX", "BY", "VARIANT"),
                     help="fixed dslash launch configuration instead of the autotuner (profiling)")
-    ap.add_argument("--workload", default="dslash", choices=["dslash", "overlap", "propagator", "learned", "project"])
+    ap.add_argument("--workload", default="dslash",
+                    choices=["dslash", "overlap", "propagator", "learned", "project", "peaks"])
     ap.add_argument("--dims", type=int, nargs=4, default=None)
     ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 32])
     ap.add_argument("--degree", type=int, default=200)
@@ -712,6 +827,8 @@ def main():
         run_learned(args)
     elif args.workload == "project":
         run_project(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_gpu(args)
 

@@ -86,7 +86,9 @@ const char* ov_last_error(const ov_ctx* ctx);
 /* Load the gauge field U_mu(n) in SU(3) (Sec. II: gluons as parallel
  * transporters on the links).  U: canonical complex128 gauge layout, host or
  * device.  The library packs it to reconstruct-12 form (rows 0 and 1 kept,
- * row 2 = conj(row0 x row1)) in FP64, FP32, FP16 and BF16.  Returns OV_EINVAL
+ * row 2 = conj(row0 x row1)) in FP32, FP16 and BF16, where the dslash is
+ * bound by bandwidth, and keeps all three rows in FP64 and double-float,
+ * where it is bound by arithmetic.  Returns OV_EINVAL
  * if any link deviates from SU(3) by more than 1e-9 (|U U^dag - 1| or the
  * reconstructed third row), since reconstruct-12 would change it. */
 int ov_set_gauge(ov_ctx* ctx, const void* U, void* stream);
@@ -147,6 +149,29 @@ int ov_get_eigenpairs(ov_ctx* ctx, int which, int* nev, double* vals, void* vecs
  * nrhs <= 16. */
 int ov_cg_solve(ov_ctx* ctx, const void* b, void* x, int nrhs, double mass, double tol, int max_iter,
                 int precond, int inner_prec, ov_solve_info* info, void* stream);
+
+/* Propagators of several quark masses from one multi-shifted CG (Sec. II,
+ * the paragraph after Eq. 8: multi-shifted CG for multiple masses, deflated
+ * by the low modes of the massless operator, Eq. 9).  With sign^2 = 1,
+ * D(m)^dag D(m) = a_m (D(0)^dag D(0) + m^2 / a_m), a_m = 1 - m^2 / (4 rho^2),
+ * so one Krylov recursion on D(0)^dag D(0) (in inner_prec, on the
+ * complement of the stored which = 1 eigenvectors, the one-sign chiral form
+ * when option "chiral" is set) serves every mass; each mass is then refined
+ * by the deflated mixed-precision CG of ov_cg_solve from that start, whose
+ * true residuals use the full D(m)^dag D(m) in the "hi_prec" precision.
+ *   b: nrhs canonical fields (host or device).  masses[nmass]: 0 <= m < 2 rho,
+ *   nmass <= 16, nrhs <= 16.
+ *   x: nmass x nrhs canonical fields ([mass][rhs], host or device), receiving
+ *   output = 0: x_k = (D(m_k)^dag D(m_k))^-1 b;
+ *   output = 1: x_k = D(m_k)^-1 b = D(m_k)^dag (D(m_k)^dag D(m_k))^-1 b;
+ *   output = 2: x_k = (1 - D/2) D(m_k)^-1 b, the quark propagator (D = D(0)/rho).
+ *   info: NULL or nmass reports; iterations count the shared recursion plus
+ *   that mass's refinement; true_residual is that of the normal equations.
+ * Returns OV_ENOTCONV (with x and info filled) if a mass misses tol within
+ * max_iter iterations of its refinement.  Allocates nmass accurate-precision
+ * fields and 2 nmass inner-precision fields for the duration of the call. */
+int ov_cg_solve_multimass(ov_ctx* ctx, const void* b, void* x, int nrhs, int nmass, const double* masses, double tol,
+                          int max_iter, int inner_prec, int output, ov_solve_info* info, void* stream);
 
 /* ---- learned preconditioner (no counterpart in the paper; used by
  * ov_cg_solve with precond = 1).  M = L2 L1, each layer
@@ -221,10 +246,25 @@ long long ov_device_bytes(const ov_ctx* ctx);
  * (instrumentation: an overlap application costs 2n+1, Sec. V). */
 long long ov_dslash_count(const ov_ctx* ctx);
 /* Capture each overlap / D^dag D application in a CUDA graph on first use
- * and replay it afterwards (enable = 1, the default; needs a non-NULL
- * stream).  Graphs are dropped whenever the polynomial, the eigenpairs or
- * a workspace pointer changes. */
+ * and replay it afterwards (enable = 1, the default).  The key is the kind
+ * of application, the two buffers, precision, nrhs and mass; the first call
+ * for a key runs eagerly and then captures, later calls replay.  A caller on
+ * the legacy default stream (NULL, which cannot be captured) gets its graphs
+ * on a library-owned stream ordered after and before its own by events; a
+ * caller whose stream is being captured gets the plain launches recorded
+ * into its own graph.  Graphs are dropped whenever the polynomial, the
+ * eigenpairs or a workspace pointer changes. */
 int ov_set_graphs(ov_ctx* ctx, int enable);
+/* Instrumentation: graphs captured and graph replays launched so far. */
+int ov_graph_stats(const ov_ctx* ctx, long long* captured, long long* replayed);
+/* Throughput of fused multiply-add on this GPU in GFLOP/s (2 flops per FMA),
+ * prec = OV_F64 or OV_F32: a kernel of independent FMA chains, 8 blocks of
+ * 256 threads per SM, best of 5 timed launches on `stream` (CUDA events).
+ * The paper has no counterpart: it is the measured denominator of the
+ * ALU-bound rooflines (the FP64 dslash is bound by the FP64 pipe on GB300,
+ * the double-float one by the FP32 pipe).  Allocates and frees one small
+ * buffer; synchronises `stream`. */
+int ov_measure_fma_peak(int prec, double* gflops, void* stream);
 /* Solver tunables:
  *   "reliable_delta" (0.1): ov_cg_solve recomputes the FP64 true residual when
  *                    the inner-precision residual has dropped by this factor;
@@ -249,8 +289,25 @@ int ov_set_graphs(ov_ctx* ctx, int enable);
  *   "proj_tc" (1):    16-bit overlap: compute eta^dag psi on the tensor cores
  *                    (0: on the CUDA cores);
  *   "net_sym" (1):    flexible CG applies the learned preconditioner as
- *                    (M + M^dag) / 2 (Hermitian) instead of M. */
+ *                    (M + M^dag) / 2 (Hermitian) instead of M;
+ *   "adaptive_delta" (0): adaptive-precision CG (Sec. V, propagator paragraph:
+ *                    adaptive CG).  > 0: the inner operator of ov_cg_solve and of
+ *                    the shared recursion of ov_cg_solve_multimass uses the
+ *                    Chebyshev interpolant of the lowest degree whose delta
+ *                    (Eq. 4, on [eps, 1]) is at most this value; every true
+ *                    residual and reliable update keeps the full polynomial, so
+ *                    the solution still meets tol with it.  0: off;
+ *   "wait_polls" (4194304): limit, in polls, of the first mbarrier wait of the
+ *                    bulk-copy dslash variants (4, 5) for their copies (also
+ *                    bounded by 2 s of the GPU timer).  When it runs out the
+ *                    block records the timeout, drains its copies with a wait
+ *                    of the full limit, writes nothing, and the call returns
+ *                    OV_ETIMEOUT; a smaller value only tests that path. */
 int ov_set_option(ov_ctx* ctx, const char* name, double value);
+/* Current value of an option of ov_set_option, or "adaptive_degree": the
+ * degree of the inner polynomial that "adaptive_delta" selected (the full
+ * degree when it is off).  OV_EINVAL for an unknown name. */
+int ov_get_option(const ov_ctx* ctx, const char* name, double* value);
 /* Launch configuration of the dslash for (prec, nrhs): block = bx sites x by
  * right-hand sides, and a register-budget variant (0: unbounded; 1, 2:
  * registers capped so that more warps are resident).  ov_tune_dslash times

@@ -59,6 +59,7 @@ _SIGS = {
     "ov_set_eigenpairs": (_I, [_P, _I, _I, _P, _P, _P]),
     "ov_get_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_I), _P, _P, _P]),
     "ov_cg_solve": (_I, [_P, _P, _P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
+    "ov_cg_solve_multimass": (_I, [_P, _P, _P, _I, _I, _P, _D, _I, _I, _I, ctypes.POINTER(SolveInfo), _P]),
     "ov_net_train": (_I, [_P, _I, _I, _D, _D, ctypes.POINTER(_D), _P]),
     "ov_net_set_weights": (_I, [_P, _P, _I]),
     "ov_net_get_weights": (_I, [_P, _P, _I]),
@@ -77,7 +78,10 @@ _SIGS = {
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
     "ov_dslash_count": (ctypes.c_longlong, [_P]),
     "ov_set_graphs": (_I, [_P, _I]),
+    "ov_graph_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "ov_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), _P]),
     "ov_set_option": (_I, [_P, ctypes.c_char_p, _D]),
+    "ov_get_option": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_D)]),
     "ov_set_dslash_shape": (_I, [_P, _I, _I, _I, _I, _I]),
     "ov_tune_dslash": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
@@ -104,6 +108,16 @@ def load(path: str = LIBPATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def measure_fma_peak(prec="f64", stream=None):
+    """GFLOP/s of fused multiply-add on the current GPU (ov_measure_fma_peak): f64 or f32."""
+    lib = load()
+    g = _D()
+    st = lib.ov_measure_fma_peak(_prec(prec), ctypes.byref(g), _stream(stream))
+    if st != 0:
+        raise OverlapError(st, "ov_measure_fma_peak failed")
+    return g.value
 
 
 def _ptr(x):
@@ -272,6 +286,21 @@ class Context:
             self._check(st)
         return info.as_dict() | {"status": st}
 
+    def cg_solve_multimass(self, b, x, masses, tol=1e-10, max_iter=3000, inner_prec="f32", output=0, stream=None,
+                           check=True):
+        """ov_cg_solve_multimass: x holds len(masses) x nrhs fields ([mass][rhs]); output 0 the
+        normal-equation solutions, 1 D(m)^-1 b, 2 the propagators (1 - D/2) D(m)^-1 b."""
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        nrhs = self._nrhs(b)
+        if _nbytes(x) != len(m) * _nbytes(b):
+            raise ValueError("x must hold len(masses) x nrhs fields")
+        infos = (SolveInfo * len(m))()
+        st = self.lib.ov_cg_solve_multimass(self.h, _ptr(b), _ptr(x), nrhs, len(m), _ptr(m), float(tol),
+                                            int(max_iter), _prec(inner_prec), int(output), infos, _stream(stream))
+        if check:
+            self._check(st)
+        return [infos[k].as_dict() | {"status": st, "mass": float(m[k])} for k in range(len(m))]
+
     # -- learned preconditioner ---------------------------------------------------------
     NET_DOUBLES = 9216
 
@@ -344,8 +373,19 @@ class Context:
     def set_graphs(self, enable):
         self._check(self.lib.ov_set_graphs(self.h, int(bool(enable))))
 
+    def graph_stats(self):
+        """(graphs captured, graph replays) so far on this context."""
+        cap, rep = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.lib.ov_graph_stats(self.h, ctypes.byref(cap), ctypes.byref(rep)))
+        return cap.value, rep.value
+
     def set_option(self, name, value):
         self._check(self.lib.ov_set_option(self.h, name.encode(), float(value)))
+
+    def get_option(self, name):
+        v = _D()
+        self._check(self.lib.ov_get_option(self.h, name.encode(), ctypes.byref(v)))
+        return v.value
 
     def set_dslash_shape(self, prec, nrhs, bx, by, variant=0):
         self._check(self.lib.ov_set_dslash_shape(self.h, _prec(prec), int(nrhs), int(bx), int(by), int(variant)))

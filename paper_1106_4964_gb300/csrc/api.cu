@@ -212,6 +212,7 @@ int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a,
     memset(&A, 0, sizeof A);
     A.g = c->g;
     A.err = c->derr + 2;
+    A.wait_polls = c->wait_polls;
     A.gauge = (const char*)c->gauge[gprec];
     A.in = in.data;
     A.in_n = in.norm;
@@ -302,8 +303,11 @@ int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_
 // Finally D(m) psi = (rho + m/2) psi + (rho - m/2) [D_w(P psi_h) / lmax + gamma5 sum_i sign(lam_i) c_i eta_i]
 // (gamma5 Q = D_w / lmax), in one more launch.
 static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out,
-                            cudaStream_t st)
+                            cudaStream_t st, int poly = 0)
 {
+    // poly 1: the inner polynomial of the adaptive-precision CG (lower degree, same [eps, 1])
+    const std::vector<double>& coef = poly ? c->coef_in : c->coef;
+    const int degree = poly ? c->degree_in : c->degree;
     if (!c->have_gauge) return set_err(c, OV_ESTATE, "overlap: no gauge field (call ov_set_gauge)");
     if (!c->have_poly) return set_err(c, OV_ESTATE, "overlap: no sign polynomial (call ov_set_sign_poly)");
     const int P = in.prec, R = in.nrhs;
@@ -347,10 +351,10 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
         double g;
     };
     BRef b1{-1, 0.0}, b2{-1, 0.0};
-    for (int k = c->degree; k >= 0; --k) {
+    for (int k = degree; k >= 0; --k) {
         const double f = k == 0 ? 0.5 : 1.0;
         if (b1.buf < 0 && b1.g == 0.0) {  // b_{k+1} = 0 (then b_{k+2} = 0 too)
-            BRef nb{-1, c->coef[k] - (b2.buf < 0 ? b2.g : 0.0)};
+            BRef nb{-1, coef[k] - (b2.buf < 0 ? b2.g : 0.0)};
             b2 = b1;
             b1 = nb;
             continue;
@@ -358,7 +362,7 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
         FieldDesc y[3];
         double sy[3];
         int ny = 1;
-        double psi_coef = c->coef[k];
+        double psi_coef = coef[k];
         const FieldDesc* hin;
         double hscale;
         if (b1.buf < 0) {
@@ -419,56 +423,97 @@ void graphs_clear(ov_ctx* c)
     c->graphs.clear();
 }
 
-// Run `body` (a fixed sequence of kernel launches on st) through a captured
-// CUDA graph: the first call for a key runs eagerly (allocating any
-// workspace) and then captures the same sequence; later calls replay it.
+// Run `body(s)` (a fixed sequence of kernel launches on stream s) through a
+// captured CUDA graph: the first call for a key runs eagerly (allocating any
+// workspace) and then captures the same sequence; later calls replay it.  The
+// legacy default stream (st == NULL) cannot be captured, so for it the graph
+// runs on a library-owned non-blocking stream ordered after st by one event
+// and followed by st through another: stream order is what the caller asked for.
 template <typename F>
 static int with_graph(ov_ctx* c, int kind, const FieldDesc& in, const FieldDesc& out, double mass, int g5,
                       cudaStream_t st, F body)
 {
-    if (!c->use_graphs || st == nullptr) return body();
+    if (!c->use_graphs) return body(st);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return body();
+    if (st != nullptr && (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone))
+        return body(st);  // the caller is capturing: record the launches into its graph
+    cudaStream_t gs = st;
+    if (st == nullptr) {
+        if (!c->gstream) {
+            OV_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+            OV_CUDA(c, cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+            OV_CUDA(c, cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+        }
+        gs = c->gstream;
+        OV_CUDA(c, cudaEventRecord(c->gev[0], st));
+        OV_CUDA(c, cudaStreamWaitEvent(gs, c->gev[0], 0));
+    }
+    auto join = [&]() -> int {
+        if (gs != st) {
+            OV_CUDA(c, cudaEventRecord(c->gev[1], gs));
+            OV_CUDA(c, cudaStreamWaitEvent(st, c->gev[1], 0));
+        }
+        return OV_OK;
+    };
     auto key = std::make_tuple(kind, (const void*)in.data, (const void*)out.data, in.prec, in.nrhs, mass, g5);
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
-        OV_CUDA(c, cudaGraphLaunch(it->second.first, st));
+        OV_CUDA(c, cudaGraphLaunch(it->second.first, gs));
         c->dslash_launches += it->second.second;
-        return OV_OK;
+        c->graph_replays++;
+        return join();
     }
-    OV_TRY(body());
+    {
+        const int s0 = body(gs);
+        if (s0 != OV_OK) {
+            join();
+            return s0;
+        }
+    }
     const long long before = c->dslash_launches;
-    OV_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int s = body();
+    OV_CUDA(c, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int s = body(gs);
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &g);
+    cudaError_t e = cudaStreamEndCapture(gs, &g);
     const long long n = c->dslash_launches - before;
     c->dslash_launches = before;
     if (s != OV_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
+        join();
         return s != OV_OK ? s : set_err(c, OV_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return set_err(c, OV_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        join();
+        return set_err(c, OV_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
     c->graphs[key] = {ex, n};
-    return OV_OK;
+    c->graph_captures++;
+    return join();
 }
 
 int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
 {
-    return with_graph(c, 0, in, out, mass, 0, st, [&]() { return overlap_apply_g5(c, in, out, mass, 0, st); });
+    return with_graph(c, 0, in, out, mass, 0, st,
+                      [&](cudaStream_t s) { return overlap_apply_g5(c, in, out, mass, 0, s); });
 }
 
-int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st)
+int overlap_g5_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out, cudaStream_t st)
+{
+    return with_graph(c, 3, in, out, mass, g5_out, st,
+                      [&](cudaStream_t s) { return overlap_apply_g5(c, in, out, mass, g5_out, s); });
+}
+
+int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st, int poly)
 {
     FieldDesc u;
     OV_TRY(ws_field(c, WS_AUX0, in.prec, in.nrhs, &u));
-    return with_graph(c, 1, in, out, mass, 0, st, [&]() {
-        OV_TRY(overlap_apply_g5(c, in, u, mass, 1, st));  // u = g5 D in
-        return overlap_apply_g5(c, u, out, mass, 1, st);  // out = g5 D g5 D in = D^dag D in
+    return with_graph(c, 1 + 16 * poly, in, out, mass, 0, st, [&](cudaStream_t s) {
+        OV_TRY(overlap_apply_g5(c, in, u, mass, 1, s, poly));  // u = g5 D in
+        return overlap_apply_g5(c, u, out, mass, 1, s, poly);  // out = g5 D g5 D in = D^dag D in
     });
 }
 
@@ -479,14 +524,14 @@ int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double ma
 // polynomial's error delta).  dcoef: device double2 [3][R] =
 // (m^2, (rho^2 - m^2/4)/rho, chi_r (rho^2 - m^2/4)/rho), per right-hand side.
 int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, const double2* dcoef,
-                 cudaStream_t st)
+                 cudaStream_t st, int poly)
 {
     FieldDesc u;
     OV_TRY(ws_field(c, WS_AUX0, in.prec, in.nrhs, &u));
-    return with_graph(c, 2, in, out, mass, 0, st, [&]() {
-        OV_TRY(overlap_apply_g5(c, in, u, 0.0, 0, st));  // u = D(0) in
+    return with_graph(c, 2 + 16 * poly, in, out, mass, 0, st, [&](cudaStream_t s) {
+        OV_TRY(overlap_apply_g5(c, in, u, 0.0, 0, s, poly));  // u = D(0) in
         FieldDesc v[3] = {in, u, u};
-        return lincomb(c, out, 3, v, nullptr, dcoef, 4, nullptr, st);
+        return lincomb(c, out, 3, v, nullptr, dcoef, 4, nullptr, s);
     });
 }
 
@@ -544,6 +589,47 @@ static void cheb_coefficients(double eps, int n, std::vector<double>& c)
         c[k] = 2.0 * s / m;
     }
     c[0] *= 0.5;
+}
+
+// delta = max over [eps, 1] of |1 - sqrt(x) P(x)| (Eq. 4) for the interpolant c, on a grid of points
+// uniform in sqrt(x) (the error oscillates fastest near eps) plus the end points
+static double poly_delta(const std::vector<double>& cf, double eps)
+{
+    const int n = (int)cf.size() - 1;
+    const int npts = 4000;
+    double worst = 0.0;
+    for (int i = 0; i <= npts; ++i) {
+        const double sx = std::sqrt(eps) + (1.0 - std::sqrt(eps)) * i / npts;
+        const double x = sx * sx;
+        const double y = (2.0 * x - (1.0 + eps)) / (1.0 - eps);
+        double b1 = 0, b2 = 0;  // Clenshaw for sum_k c_k T_k(y)
+        for (int k = n; k >= 1; --k) {
+            const double b0 = cf[k] + 2.0 * y * b1 - b2;
+            b2 = b1;
+            b1 = b0;
+        }
+        const double P = cf[0] + y * b1 - b2;
+        worst = std::max(worst, std::fabs(1.0 - sx * P));
+    }
+    return worst;
+}
+
+// Inner polynomial of the adaptive-precision CG: the lowest degree (<= the accurate one) whose delta on
+// [eps, 1] is at most c->adaptive_delta; off (degree_in = degree) when adaptive_delta is 0.
+static void set_inner_poly(ov_ctx* c)
+{
+    c->degree_in = c->degree;
+    c->coef_in = c->coef;
+    if (!(c->adaptive_delta > 0)) return;
+    std::vector<double> cf;
+    for (int n = 1; n < c->degree; ++n) {
+        cheb_coefficients(c->eps, n, cf);
+        if (poly_delta(cf, c->eps) <= c->adaptive_delta) {
+            c->degree_in = n;
+            c->coef_in = cf;
+            return;
+        }
+    }
 }
 
 static int check_prec(ov_ctx* c, int prec)
@@ -618,6 +704,9 @@ int ov_destroy(ov_ctx* c)
         if (c->stage[i]) dev_free(c, c->stage[i], c->stage_bytes[i]);
     dev_free(c, c->dscal, DSCAL_DOUBLES * sizeof(double));
     dev_free(c, c->derr, 64);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    for (auto& e : c->gev)
+        if (e) cudaEventDestroy(e);
     delete c;
     return OV_OK;
 }
@@ -729,6 +818,7 @@ int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambd
     c->eps = eps;
     c->degree = degree;
     cheb_coefficients(eps, degree, c->coef);
+    set_inner_poly(c);
     if (lambda_max > 0) {
         c->lmax = lambda_max;
     } else {
@@ -849,6 +939,50 @@ int ov_cg_solve(ov_ctx* c, const void* b, void* x, int nrhs, double mass, double
     if (s != OV_OK && s != OV_ENOTCONV && s != OV_ESTALL) return s;
     OV_CUDA(c, launch_unpack(c->g, fx, dx, 0, st));
     OV_TRY(stage_out_finish(c, x, dx, bytes, st));
+    return s;
+}
+
+int ov_cg_solve_multimass(ov_ctx* c, const void* b, void* x, int nrhs, int nmass, const double* masses, double tol,
+                          int max_iter, int inner_prec, int output, ov_solve_info* info, void* stream)
+{
+    if (!c) return OV_EINVAL;
+    if (!b || !x || !masses) return set_err(c, OV_EINVAL, "null buffer");
+    if (nrhs < 1 || nrhs > 16) return set_err(c, OV_EINVAL, "nrhs = %d out of range 1..16", nrhs);
+    if (nmass < 1 || nmass > 16) return set_err(c, OV_EINVAL, "nmass = %d out of range 1..16", nmass);
+    if (!(tol > 0) || max_iter < 1) return set_err(c, OV_EINVAL, "tol and max_iter must be positive");
+    if (output < 0 || output > 2) return set_err(c, OV_EINVAL, "output = %d (0, 1 or 2)", output);
+    for (int k = 0; k < nmass; ++k)
+        if (!(masses[k] >= 0 && masses[k] < 2 * c->rho)) return set_err(c, OV_EINVAL, "mass %g outside [0, 2 rho)", masses[k]);
+    OV_TRY(check_prec(c, inner_prec));
+    if (!c->have_gauge || !c->have_poly) return set_err(c, OV_ESTATE, "multimass: needs gauge field and sign polynomial");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t one = (size_t)nrhs * 2 * c->g.Vh * 12 * 16;
+    const double* db = nullptr;
+    OV_TRY(stage_in(c, 0, b, one, st, &db));
+    FieldDesc fb;
+    OV_TRY(ws_field(c, WS_CG_B, P_F64, nrhs, &fb));
+    OV_CUDA(c, launch_pack(c->g, db, fb, 0, st));
+    // one accurate-precision solution field per mass (device memory for the duration of the call)
+    std::vector<FieldDesc> fx(nmass);
+    int s = OV_OK;
+    for (int k = 0; k < nmass && s == OV_OK; ++k) s = field_alloc(c, c->hi_prec, nrhs, &fx[k]);
+    if (s == OV_OK) s = multimass_impl(c, fb, fx.data(), nmass, masses, tol, max_iter, inner_prec, output, info, st);
+    if (s == OV_OK || s == OV_ENOTCONV) {
+        FieldDesc f64;
+        int s2 = ws_field(c, WS_CG_X, P_F64, nrhs, &f64);
+        for (int k = 0; k < nmass && s2 == OV_OK; ++k) {
+            double* dx = nullptr;
+            void* hx = (char*)x + one * k;
+            s2 = stage_out_buffer(c, 1, hx, one, &dx);
+            if (s2 == OV_OK) s2 = convert(c, fx[k], f64, st);
+            if (s2 == OV_OK && launch_unpack(c->g, f64, dx, 0, st) != cudaSuccess)
+                s2 = set_err(c, OV_ECUDA, "multimass: unpack failed");
+            if (s2 == OV_OK) s2 = stage_out_finish(c, hx, dx, one, st);
+        }
+        if (s2 != OV_OK) s = s2;
+    }
+    cudaStreamSynchronize(st);
+    for (auto& f : fx) field_free(c, &f);
     return s;
 }
 
@@ -975,6 +1109,14 @@ long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
 
 long long ov_dslash_count(const ov_ctx* c) { return c ? c->dslash_launches : -1; }
 
+int ov_graph_stats(const ov_ctx* c, long long* captured, long long* replayed)
+{
+    if (!c) return OV_EINVAL;
+    if (captured) *captured = c->graph_captures;
+    if (replayed) *replayed = c->graph_replays;
+    return OV_OK;
+}
+
 int ov_set_option(ov_ctx* c, const char* name, double value)
 {
     if (!c || !name) return c ? set_err(c, OV_EINVAL, "null option name") : OV_EINVAL;
@@ -995,12 +1137,41 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
         c->net_sym = value != 0;
     } else if (n == "chiral") {
         c->chiral = value != 0;
+    } else if (n == "adaptive_delta") {
+        if (!(value >= 0 && value < 1)) return set_err(c, OV_EINVAL, "adaptive_delta must lie in [0, 1)");
+        graphs_clear(c);
+        c->adaptive_delta = value;
+        if (c->have_poly) set_inner_poly(c);
+    } else if (n == "wait_polls") {
+        if (!(value >= 0 && value <= (double)DSLASH_WAIT_POLLS))
+            return set_err(c, OV_EINVAL, "wait_polls must lie in [0, %lld]", DSLASH_WAIT_POLLS);
+        graphs_clear(c);
+        c->wait_polls = (long long)value;
     } else if (n == "hi_prec") {
         if (value != P_F64 && value != P_DF64) return set_err(c, OV_EINVAL, "hi_prec must be OV_F64 or OV_DF64");
         c->hi_prec = (int)value;
     } else {
         return set_err(c, OV_EINVAL, "unknown option '%s'", name);
     }
+    return OV_OK;
+}
+
+int ov_get_option(const ov_ctx* c, const char* name, double* value)
+{
+    if (!c || !name || !value) return OV_EINVAL;
+    const std::string n(name);
+    if (n == "reliable_delta") *value = c->reliable_delta;
+    else if (n == "filter_hw") *value = c->filter_hw;
+    else if (n == "filter_dd") *value = c->filter_dd;
+    else if (n == "eig_prec") *value = c->eig_prec;
+    else if (n == "proj_tc") *value = c->proj_tc;
+    else if (n == "net_sym") *value = c->net_sym;
+    else if (n == "chiral") *value = c->chiral;
+    else if (n == "hi_prec") *value = c->hi_prec;
+    else if (n == "wait_polls") *value = (double)c->wait_polls;
+    else if (n == "adaptive_delta") *value = c->adaptive_delta;
+    else if (n == "adaptive_degree") *value = c->degree_in;
+    else return OV_EINVAL;
     return OV_OK;
 }
 

@@ -122,7 +122,7 @@ __device__ __forceinline__ void store_link(char* base, int Vh, int s, const doub
     } else if constexpr (P == P_F64) {
         double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) b[(size_t)k * Vh + s] = make_double2(u[2 * k], u[2 * k + 1]);
+        for (int k = 0; k < 9; ++k) b[(size_t)k * Vh + s] = make_double2(u[2 * k], u[2 * k + 1]);
     } else if constexpr (P == P_F32) {
         float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll

@@ -65,6 +65,10 @@ struct ov_ctx {
     double rho = 1.5, eps = 0.05, lmax = 0.0;
     int degree = 0;
     std::vector<double> coef;
+    // adaptive-precision CG: the inner operator's polynomial (degree_in <= degree, delta <= adaptive_delta)
+    double adaptive_delta = 0.0;
+    int degree_in = 0;
+    std::vector<double> coef_in;
     bool have_poly = false;
 
     ov::EigSet eig[2];
@@ -86,6 +90,11 @@ struct ov_ctx {
     std::map<std::tuple<int, const void*, const void*, int, int, double, int>, std::pair<cudaGraphExec_t, long long>>
         graphs;
     bool use_graphs = true;
+    long long graph_captures = 0, graph_replays = 0;  // instrumentation (ov_graph_stats)
+    // library-owned stream (and its two ordering events) on which graphs run for callers that pass the
+    // legacy default stream, which cannot be captured
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
 
     // instrumentation: number of dslash launches issued through this context
     long long dslash_launches = 0;
@@ -99,6 +108,7 @@ struct ov_ctx {
     int net_sym = 1;              // learned preconditioner applied as (M + M^dag) / 2
     int hi_prec = ov::P_F64;      // accurate arithmetic of the solvers: P_F64 or P_DF64
     int chiral = 0;               // ov_cg_solve: inner operator restricted to one chiral sector
+    long long wait_polls = ov::DSLASH_WAIT_POLLS;  // first bounded wait of the bulk-copy dslash (option "wait_polls")
 
     // tensor-core projection buffers (proj_tc.cu)
     void* tc_b = nullptr;
@@ -145,10 +155,12 @@ int eig_vectors(ov_ctx* c, int which, int prec, cudaStream_t st, FieldDesc* out)
 int dslash_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double a, double b, int g5_core, int g5_out,
                  int ny, const FieldDesc* y, const double* sy, cudaStream_t st, int gprec = -1);
 int overlap_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
-// out = D(m)^dag D(m) in
-int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st);
+// out = gamma5^g5_out D(m) in (graph-captured like overlap_apply)
+int overlap_g5_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out, cudaStream_t st);
+// out = D(m)^dag D(m) in; poly 1: with the inner polynomial of the adaptive-precision CG
+int normal_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, cudaStream_t st, int poly = 0);
 int chiral_apply(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, const double2* dcoef,
-                 cudaStream_t st);
+                 cudaStream_t st, int poly = 0);
 int chiral_setup(ov_ctx* c, const FieldDesc& f, const FieldDesc& tmp, double mass, cudaStream_t st);
 
 // level-1 helpers (stream-ordered); results of reductions land in device memory
@@ -162,8 +174,12 @@ int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_
 // solvers (solver.cu)
 int estimate_lambda_max(ov_ctx* c, int steps, double* lmax, cudaStream_t st);
 int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st);
+// warm: x holds the starting iterate (else the solve starts from x = 0)
 int cg_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc& x, double mass, double tol, int max_iter, int precond,
-            int inner_prec, ov_solve_info* info, cudaStream_t st);
+            int inner_prec, ov_solve_info* info, cudaStream_t st, bool warm = false);
+// one multi-shifted CG for several masses, then a per-mass refinement (solver.cu)
+int multimass_impl(ov_ctx* c, const FieldDesc& b, const FieldDesc* x, int nmass, const double* masses, double tol,
+                   int max_iter, int inner_prec, int output, ov_solve_info* info, cudaStream_t st);
 void net_free(ov_ctx* c);
 
 // eigenpairs

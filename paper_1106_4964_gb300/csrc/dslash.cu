@@ -499,10 +499,10 @@ __device__ __forceinline__ void tma_expect(uint64_t* b, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool tma_wait(uint64_t* b)
+__device__ __forceinline__ bool tma_wait(uint64_t* b, long long polls)
 {
     const unsigned long long t0 = global_ns();
-    for (long long i = 0; i < TMA_SPIN; ++i) {
+    for (long long i = 0; i < polls; ++i) {
         if ((i & 1023) == 1023 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
         uint32_t ok;
         asm volatile(
@@ -678,10 +678,11 @@ __global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashA
             }
         }
     }
-    if (!tma_wait(bar)) {
-        // the copies never completed: report, give them one more bounded wait, write nothing
+    if (!tma_wait(bar, A.wait_polls)) {
+        // the copies did not complete within the first wait's limit: report, drain them with a wait of the
+        // full limit (no block exits with bulk copies in flight), write nothing
         if (A.err) atomicExch(A.err, 1u);
-        tma_wait(bar);
+        tma_wait(bar, TMA_SPIN);
         return;
     }
     if (s >= g.Vh) return;

@@ -14,10 +14,10 @@
 // (spin, colour, re/im) and packed as 12 double2 (FP64), 6 float4 (FP32) or
 // 3 x 8 16-bit values (FP16 / BF16) with one FP32 scale per site
 // (norm[r][p][s] = max |component|, values stored divided by it).
-// Gauge links keep only rows 0 and 1 of each SU(3) matrix (reconstruct-12),
-// forward links only: link[p][mu][k][s] = U_mu(n), n = site (p, s); chunks
-// are 6 double2 (FP64), 3 float4 (FP32) or 3 x 4 16-bit values; double-float
-// keeps all three rows, 9 float4 (hi, lo, hi, lo).
+// Gauge links: forward links only; FP32 and 16-bit keep only rows 0 and 1 of
+// each SU(3) matrix (reconstruct-12): link[p][mu][k][s] = U_mu(n), n = site (p, s); chunks
+// are 3 float4 (FP32) or 3 x 4 16-bit values; FP64 and double-float keep all
+// three rows, 9 double2 (FP64) or 9 float4 (hi, lo, hi, lo).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -43,16 +43,15 @@ inline bool wide(int prec) { return prec == P_F64 || prec == P_DF64; }
 inline int spinor_chunks(int prec) { return wide(prec) ? 12 : (prec == P_F32 ? 6 : 3); }
 inline bool has_norm(int prec) { return prec == P_F16 || prec == P_BF16; }
 inline size_t spinor_site_bytes(int prec) { return (size_t)spinor_chunks(prec) * 16; }
-// links: reconstruct-12 (rows 0 and 1), except double-float, which keeps all 18 reals (its
-// row-2 reconstruction would cost more arithmetic than the extra 48 bytes cost bandwidth)
-inline size_t gauge_link_bytes(int prec)
-{
-    return prec == P_DF64 ? 144 : (prec == P_F64 ? 96 : (prec == P_F32 ? 48 : 24));
-}
+// links: reconstruct-12 (rows 0 and 1) in FP32 and 16 bits, where bandwidth bounds the dslash; FP64
+// and double-float keep all 18 reals: their dslash is bound by arithmetic (GB300's FP64 pipe is a
+// small fraction of its FP32 pipe, double-float costs ~10 FP32 operations per operation), and the
+// row-2 reconstruction would cost about a fifth of their arithmetic to save bandwidth they do not use
+inline size_t gauge_link_bytes(int prec) { return wide(prec) ? 144 : (prec == P_F32 ? 48 : 24); }
 template <int P>
 __host__ __device__ constexpr size_t gauge_link_bytes_dev()
 {
-    return P == P_DF64 ? 144 : (P == P_F64 ? 96 : (P == P_F32 ? 48 : 24));
+    return (P == P_DF64 || P == P_F64) ? 144 : (P == P_F32 ? 48 : 24);
 }
 template <int P>
 __host__ __device__ constexpr int nchunk_dev() { return (P == P_F64 || P == P_DF64) ? 12 : (P == P_F32 ? 6 : 3); }
@@ -449,6 +448,14 @@ __device__ __forceinline__ void load_link(const char* __restrict__ base, int Vh,
             float4 t = __ldg(b + (size_t)k * Vh + s);
             u[2 * k] = from_df<Real>(df64(t.x, t.y));
             u[2 * k + 1] = from_df<Real>(df64(t.z, t.w));
+        }
+    } else if constexpr (P == P_F64) {  // stored third row (9 chunks per link)
+        const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+        for (int k = 6; k < 9; ++k) {
+            double2 t = __ldg(b + (size_t)k * Vh + s);
+            u[2 * k] = (Real)t.x;
+            u[2 * k + 1] = (Real)t.y;
         }
     } else {
         link_row2<Real>(u);

@@ -24,7 +24,9 @@ struct DslashArgs {
     int nrhs;
     int g5_core, g5_out;
     unsigned* err;               // set to 1 when a bounded wait of a staged variant times out
+    long long wait_polls;        // limit of the bulk-copy variants' first mbarrier wait (polls)
 };
+constexpr long long DSLASH_WAIT_POLLS = 1ll << 22;  // default first-wait limit (also bounded by 2 s)
 // var: 0 unbounded registers, 1 and 2 capped for occupancy, 3 per-thread cp.async staging
 // (FP32 math, by = 1), 4 block-wide bulk-copy (TMA) staging of the neighbour ranges (FP32 math;
 // fixed 128-site blocks, bx and by ignored), 5 the same with the eight links loaded before the wait,

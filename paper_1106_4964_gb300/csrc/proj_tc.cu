@@ -361,7 +361,10 @@ int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cuda
         c->tc_err = (int*)p;
         OV_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), st));
     }
-    OV_CUDA(c, cudaFuncSetAttribute(proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // once per process, for the largest ring (npad = 256): no attribute call inside a graph capture
+    static const cudaError_t attr = cudaFuncSetAttribute(proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         TC_STAGES * (TC_M + 256) * TC_BK * 2 + 1024);
+    OV_CUDA(c, attr);
     const int tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : (npad <= 128 ? 128 : 256));
     proj_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ktiles, npad, tmem_cols, (float*)c->partials, c->tc_err);
     OV_CUDA(c, cudaGetLastError());

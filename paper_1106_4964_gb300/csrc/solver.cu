@@ -712,7 +712,7 @@ bool net_ready(const ov_ctx* c);
 int net_record_pair(ov_ctx* c, const FieldDesc& r64, const FieldDesc& x64, cudaStream_t st);
 
 int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mass, double tol, int max_iter,
-            int precond, int inner_prec, ov_solve_info* info, cudaStream_t st)
+            int precond, int inner_prec, ov_solve_info* info, cudaStream_t st, bool warm)
 {
     auto t0 = std::chrono::steady_clock::now();
     const int R = b_in.nrhs;
@@ -728,6 +728,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
         OV_TRY(ws_field(c, WS_CG_BH, Ph, R, &b));
         OV_TRY(ws_field(c, WS_CG_XH, Ph, R, &x));
         OV_TRY(convert(c, b_in, b, st));
+        if (warm) OV_TRY(convert(c, x_out, x, st));
     }
     FieldDesc r, t, rs, ps, qs, xs, xt, zs, rold;
     OV_TRY(ws_field(c, WS_CG_R, Ph, R, &r));
@@ -782,8 +783,11 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // (b^dag gamma5 b = +-|b|^2); the true residuals keep the full D^dag D
     const double2* dch = (const double2*)(c->dscal + DSCAL_CHCO);
     if (c->chiral) OV_TRY(chiral_setup(c, b, t, mass, st));
+    // adaptive precision (Sec. V: adaptive CG): the inner operator may use a lower-degree polynomial; the
+    // reliable updates recompute the true residual with the accurate one
+    const int ipoly = c->adaptive_delta > 0 ? 1 : 0;
     auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-        return c->chiral ? chiral_apply(c, in, out, mass, dch, st) : normal_apply(c, in, out, mass, st);
+        return c->chiral ? chiral_apply(c, in, out, mass, dch, st, ipoly) : normal_apply(c, in, out, mass, st, ipoly);
     };
     // In chiral mode every vector of the inner recursion must stay in its right-hand side's sector:
     // the one-sign operator acts on the other sector as m^2 (plus a coupling back), so rounding-level
@@ -869,7 +873,7 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
         return OV_OK;
     };
 
-    OV_CUDA(c, cudaMemsetAsync(x.data, 0, x.rhs_bytes() * R, st));
+    if (!warm) OV_CUDA(c, cudaMemsetAsync(x.data, 0, x.rhs_bytes() * R, st));
     bool all_done = false;
     OV_TRY(refresh(all_done));
     const double delta = c->reliable_delta;  // reliable-update trigger: residual drop since the last update
@@ -1017,6 +1021,288 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     for (int q = 0; q < R; ++q) ok = ok && res[q] <= tol;
     if (!ok) return set_err(c, OV_ENOTCONV, "cg: not converged after %d iterations", iters);
     return OV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// multi-mass solve (Sec. II: one multi-shifted CG for the propagators of several masses)
+// ---------------------------------------------------------------------------
+// With sign^2 = 1, D(m)^dag D(m) = a_m (D(0)^dag D(0) + s_m), a_m = 1 - m^2 / (4 rho^2), s_m = m^2 / a_m
+// (Eq. 8 and D^dag D = rho (D + D^dag)), so every mass shares the Krylov space of D(0)^dag D(0).  Step 1:
+// on the complement of the stored D^dag D modes xi_i, the shifted systems (A0 + s_k) y_k = b_h are solved by
+// one CG recursion on A0 in the inner precision, whose shifted residuals are collinear with the base
+// residual, r_k = z_k r (shifted-system CG, Jegerlehner 1996); each (mass, right-hand side) stops once
+// |z_k| |r| <= tol_in |b_h|.  Step 2: x_k = y_k / a_k + sum_i xi_i (xi_i^dag b) / (a_k mu_i + m_k^2) (Eq. 9)
+// in the accurate precision.  Step 3: the identity above holds only up to the polynomial's error, so each
+// mass is refined by the deflated mixed-precision CG with reliable updates (cg_impl, warm start), whose
+// true residuals use the full two-sign D(m_k)^dag D(m_k).  Output 1 turns x_k into D(m_k)^-1 b =
+// D(m_k)^dag x_k = gamma5 D(m_k) gamma5 x_k, output 2 into the propagator (1 - D/2) D(m_k)^-1 b with
+// D = D(0)/rho, computed as z - D(0) z / (2 rho).
+int multimass_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc* xout, int nmass, const double* masses,
+                   double tol, int max_iter, int inner_prec, int output, ov_solve_info* info, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int R = b_in.nrhs, M = nmass, Ps = inner_prec, Ph = c->hi_prec;
+    const double rho = c->rho;
+    EigSet& X = c->eig[1];
+    const int nd = X.nev;
+    if ((size_t)(2 * M + 2) * R * 2 > (size_t)(DSCAL_NORM - DSCAL_CGCO) || (size_t)2 * nd * R * 2 > DSCAL_COEF)
+        return set_err(c, OV_EINVAL, "multimass: too many masses, right-hand sides or modes");
+    std::vector<double> am(M), sm(M);
+    for (int k = 0; k < M; ++k) {
+        am[k] = 1.0 - masses[k] * masses[k] / (4.0 * rho * rho);
+        if (!(am[k] > 0)) return set_err(c, OV_EINVAL, "multimass: mass %g >= 2 rho", masses[k]);
+        sm[k] = masses[k] * masses[k] / am[k];
+    }
+    // work fields: accurate b, inner r, p, q, and per mass p_k, y_k
+    FieldDesc b = b_in, r, p, q;
+    if (b_in.prec != Ph) {
+        OV_TRY(ws_field(c, WS_CG_BH, Ph, R, &b));
+        OV_TRY(convert(c, b_in, b, st));
+    }
+    OV_TRY(ws_field(c, WS_CG_RS, Ps, R, &r));
+    OV_TRY(ws_field(c, WS_CG_PS, Ps, R, &p));
+    OV_TRY(ws_field(c, WS_CG_QS, Ps, R, &q));
+    std::vector<FieldDesc> pk(M), yk(M);
+    int status = OV_OK;
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (auto& f : pk) field_free(c, &f);
+        for (auto& f : yk) field_free(c, &f);
+    };
+#define MM_TRY(x)              \
+    do {                       \
+        int s__ = (x);         \
+        if (s__ != OV_OK) {    \
+            release();         \
+            return s__;        \
+        }                      \
+    } while (0)
+    for (int k = 0; k < M; ++k) {
+        MM_TRY(field_alloc(c, Ps, R, &pk[k]));
+        MM_TRY(field_alloc(c, Ps, R, &yk[k]));
+    }
+    FieldDesc xi64{}, xis{};
+    if (nd) {
+        MM_TRY(eig_vectors(c, 1, Ph, st, &xi64));
+        MM_TRY(eig_vectors(c, 1, Ps, st, &xis));
+    }
+    double2* dco = (double2*)(c->dscal + DSCAL_CGCO);
+    double2* ddt = (double2*)(c->dscal + DSCAL_DOT);
+    double* dnr = c->dscal + DSCAL_NORM;
+    // low-mode coefficients pb[i][q] = xi_i^dag b_q, and b_h = b - sum_i xi_i pb_i
+    std::vector<double2> pb((size_t)nd * R);
+    FieldDesc bh;
+    MM_TRY(ws_field(c, WS_CG_T, Ph, R, &bh));
+    MM_TRY(copy_field(c, b, bh, st));
+    if (nd) {
+        MM_TRY(block_dots(c, xi64, nd, b, st));
+        MM_TRY(to_host(c, c->dscal, pb.data(), pb.size() * sizeof(double2), st));
+        MM_TRY(block_sub(c, xi64, nd, bh, st));
+    }
+    // chiral mode: the inner operator A0 is the one-sign form on each source's sector
+    if (c->chiral) MM_TRY(chiral_setup(c, bh, q, 0.0, st));
+    const double2* dch = (const double2*)(c->dscal + DSCAL_CHCO);
+    const int ipoly = c->adaptive_delta > 0 ? 1 : 0;
+    auto A0 = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+        return c->chiral ? chiral_apply(c, in, out, 0.0, dch, st, ipoly) : normal_apply(c, in, out, 0.0, st, ipoly);
+    };
+    MM_TRY(convert(c, bh, r, st));
+    MM_TRY(copy_field(c, r, p, st));
+    for (int k = 0; k < M; ++k) {
+        MM_TRY(copy_field(c, r, pk[k], st));
+        MM_TRY(cudaMemsetAsync(yk[k].data, 0, yk[k].rhs_bytes() * R, st) == cudaSuccess ? OV_OK : OV_ECUDA);
+        if (yk[k].norm) MM_TRY(cudaMemsetAsync(yk[k].norm, 0, (size_t)2 * yk[k].Vh * 4 * R, st) == cudaSuccess ? OV_OK : OV_ECUDA);
+    }
+    std::vector<double> rr(R), bhn(R);
+    {
+        std::vector<double2> h(R);
+        MM_TRY(norm2(c, r, (double*)ddt, st));
+        MM_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+        for (int j = 0; j < R; ++j) rr[j] = bhn[j] = h[j].x;
+        for (int j = 0; j < R; ++j) bhn[j] = std::sqrt(bhn[j]);
+    }
+    // the inner precision cannot resolve residuals below its rounding: the shifted solve stops there and
+    // the refinement (FP64 or double-float true residuals) finishes the job
+    const double tol_in = std::max(tol, wide(Ps) ? tol : (Ps == P_F32 ? 1e-6 : 1e-3));
+    // shifted-CG scalars per (mass, rhs): z, z_old, and the base recursion's alpha_old, beta_old per rhs
+    std::vector<double> z((size_t)M * R, 1.0), zo((size_t)M * R, 1.0), zn((size_t)M * R, 1.0);
+    std::vector<double> aold(R, 1.0), bold(R, 0.0);
+    std::vector<char> active((size_t)M * R, 1);
+    for (int j = 0; j < R; ++j)
+        if (!(bhn[j] > 0))
+            for (int k = 0; k < M; ++k) active[(size_t)k * R + j] = 0;  // b in span(xi): the low modes solve it
+    int iters = 0;
+    std::vector<double2> co((size_t)(2 * M + 2) * R);
+    while (iters < max_iter) {
+        bool any = false;
+        for (char a : active) any = any || a;
+        if (!any) break;
+        MM_TRY(A0(p, q));
+        if (nd) {  // q <- (1 - sum xi xi^dag) q: the recursion stays on the deflated complement
+            MM_TRY(block_dots(c, xis, nd, q, st));
+            MM_TRY(block_sub(c, xis, nd, q, st));
+        }
+        std::vector<double2> h(R);
+        MM_TRY(dot(c, p, q, ddt, st));
+        MM_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+        std::vector<double> alpha(R, 0.0);
+        for (int j = 0; j < R; ++j) {
+            bool live = false;
+            for (int k = 0; k < M; ++k) live = live || active[(size_t)k * R + j];
+            alpha[j] = (live && h[j].x > 0) ? rr[j] / h[j].x : 0.0;
+            if (!std::isfinite(alpha[j])) {
+                release();
+                return set_err(c, OV_ENAN, "multimass: NaN/Inf in the recursion");
+            }
+        }
+        // y_k += alpha_k p_k, alpha_k = alpha z_k' / z_k (coefficient blocks [k][2][R])
+        for (int k = 0; k < M; ++k)
+            for (int j = 0; j < R; ++j) {
+                const size_t kj = (size_t)k * R + j;
+                zn[kj] = z[kj];
+                double ak = 0.0;
+                if (active[kj] && alpha[j] != 0.0) {
+                    zn[kj] = z[kj] * zo[kj] * aold[j] /
+                             (alpha[j] * bold[j] * (zo[kj] - z[kj]) + zo[kj] * aold[j] * (1.0 + sm[k] * alpha[j]));
+                    ak = alpha[j] * zn[kj] / z[kj];
+                }
+                co[(size_t)(2 * k) * R + j] = make_double2(1, 0);
+                co[(size_t)(2 * k + 1) * R + j] = make_double2(ak, 0);
+            }
+        // r -= alpha q (with |r|^2)
+        for (int j = 0; j < R; ++j) {
+            co[(size_t)(2 * M) * R + j] = make_double2(1, 0);
+            co[(size_t)(2 * M + 1) * R + j] = make_double2(-alpha[j], 0);
+        }
+        MM_TRY(to_dev(c, co.data(), dco, co.size() * sizeof(double2), st));
+        for (int k = 0; k < M; ++k) {
+            FieldDesc v[2] = {yk[k], pk[k]};
+            MM_TRY(lincomb(c, yk[k], 2, v, nullptr, dco + (size_t)(2 * k) * R, 0, nullptr, st));
+        }
+        {
+            FieldDesc v[2] = {r, q};
+            MM_TRY(lincomb(c, r, 2, v, nullptr, dco + (size_t)(2 * M) * R, 0, dnr, st));
+        }
+        std::vector<double> rn(R);
+        MM_TRY(to_host(c, dnr, rn.data(), R * sizeof(double), st));  // also orders the coefficient reuse below
+        ++iters;
+        std::vector<double> beta(R, 0.0);
+        for (int j = 0; j < R; ++j) {
+            if (!std::isfinite(rn[j])) {
+                release();
+                return set_err(c, OV_ENAN, "multimass: NaN/Inf in the residual");
+            }
+            beta[j] = (alpha[j] != 0.0 && rr[j] > 0) ? rn[j] / rr[j] : 0.0;
+        }
+        // p_k = z_k' r + beta_k p_k, beta_k = beta (z_k' / z_k)^2; a finished (mass, rhs) keeps p_k, y_k
+        for (int k = 0; k < M; ++k)
+            for (int j = 0; j < R; ++j) {
+                const size_t kj = (size_t)k * R + j;
+                double zr = 0.0, bk = 1.0;
+                if (active[kj] && alpha[j] != 0.0) {
+                    zr = zn[kj];
+                    bk = beta[j] * (zn[kj] / z[kj]) * (zn[kj] / z[kj]);
+                    if (std::fabs(zn[kj]) * std::sqrt(rn[j]) <= tol_in * bhn[j]) active[kj] = 0;
+                }
+                co[(size_t)(2 * k) * R + j] = make_double2(zr, 0);
+                co[(size_t)(2 * k + 1) * R + j] = make_double2(bk, 0);
+                if (zn[kj] != z[kj]) {
+                    zo[kj] = z[kj];
+                    z[kj] = zn[kj];
+                }
+            }
+        for (int j = 0; j < R; ++j) {
+            co[(size_t)(2 * M) * R + j] = make_double2(1, 0);
+            co[(size_t)(2 * M + 1) * R + j] = make_double2(alpha[j] != 0.0 ? beta[j] : 1.0, 0);
+            if (alpha[j] != 0.0) {
+                aold[j] = alpha[j];
+                bold[j] = beta[j];
+                rr[j] = rn[j];
+            }
+        }
+        MM_TRY(to_dev(c, co.data(), dco, co.size() * sizeof(double2), st));
+        for (int k = 0; k < M; ++k) {
+            FieldDesc v[2] = {r, pk[k]};
+            MM_TRY(lincomb(c, pk[k], 2, v, nullptr, dco + (size_t)(2 * k) * R, 0, nullptr, st));
+        }
+        {
+            FieldDesc v[2] = {r, p};
+            MM_TRY(lincomb(c, p, 2, v, nullptr, dco + (size_t)(2 * M) * R, 0, nullptr, st));
+        }
+        if (c->chiral) {  // keep the recursion on each source's sector (rounding leaks out of it)
+            FieldDesc v2[2] = {p, p};
+            MM_TRY(lincomb(c, p, 2, v2, nullptr, dch + 3 * R, 2, nullptr, st));
+        }
+        if (verbose() && iters % 50 == 0) {
+            double w = 0;
+            for (int j = 0; j < R; ++j) w = std::max(w, std::sqrt(rn[j]) / bhn[j]);
+            fprintf(stderr, "[ov] multimass iteration %d: base residual %.3e\n", iters, w);
+        }
+    }
+    // x_k = y_k / a_k + sum_i xi_i pb_i / (a_k mu_i + m_k^2) in the accurate precision
+    FieldDesc xt;
+    MM_TRY(ws_field(c, WS_CG_U, Ph, R, &xt));
+    for (int k = 0; k < M; ++k) {
+        MM_TRY(convert(c, yk[k], xt, st));
+        const double2 hs = make_double2(1.0 / am[k], 0);
+        MM_TRY(lincomb(c, xout[k], 1, &xt, &hs, nullptr, 0, nullptr, st));
+        if (nd) {
+            std::vector<double2> cx((size_t)nd * R);
+            for (int i = 0; i < nd; ++i) {
+                const double muk = am[k] * X.vals[i] + masses[k] * masses[k];
+                const double inv = muk > 1e-10 * (am[k] * X.vals[nd - 1] + masses[k] * masses[k]) ? 1.0 / muk : 0.0;
+                for (int j = 0; j < R; ++j) {
+                    const double2 v = pb[(size_t)i * R + j];
+                    cx[(size_t)i * R + j] = make_double2(-v.x * inv, -v.y * inv);  // proj_update subtracts
+                }
+            }
+            MM_TRY(to_dev(c, cx.data(), c->dscal, cx.size() * sizeof(double2), st));
+            FieldDesc none{};
+            MM_TRY(launch_proj_update(c->g, xi64, nd, (const double2*)c->dscal, nullptr, xout[k], xout[k], none, st) ==
+                           cudaSuccess
+                       ? OV_OK
+                       : OV_ECUDA);
+            MM_TRY(cudaStreamSynchronize(st) == cudaSuccess ? OV_OK : OV_ECUDA);
+        }
+    }
+    release();
+#undef MM_TRY
+    // refinement per mass (warm start), then the requested output
+    int worst = OV_OK;
+    for (int k = 0; k < M; ++k) {
+        ov_solve_info inf{};
+        const int left = std::max(1, max_iter - iters);
+        int sk = cg_impl(c, b_in, xout[k], masses[k], tol, left, 0, Ps, &inf, st, true);
+        if (sk != OV_OK && sk != OV_ENOTCONV) return sk;
+        if (sk != OV_OK) worst = sk;
+        if (info) {
+            info[k] = inf;
+            info[k].iterations += iters;
+        }
+        if (output >= 1) {
+            // z = D(m)^dag x = gamma5 D(m) gamma5 x
+            FieldDesc t1, t2;
+            OV_TRY(ws_field(c, WS_AUX1, xout[k].prec, R, &t1));
+            OV_TRY(ws_field(c, WS_CG_U, xout[k].prec, R, &t2));
+            const double2 one = make_double2(1, 0);
+            OV_TRY(lincomb(c, t1, 1, &xout[k], &one, nullptr, 1, nullptr, st));  // t1 = gamma5 x
+            if (output == 1) {
+                OV_TRY(overlap_g5_apply(c, t1, xout[k], masses[k], 1, st));
+            } else {
+                OV_TRY(overlap_g5_apply(c, t1, t2, masses[k], 1, st));   // t2 = z
+                OV_TRY(overlap_apply(c, t2, t1, 0.0, st));                      // t1 = D(0) z
+                FieldDesc v[2] = {t2, t1};
+                const double2 h[2] = {make_double2(1, 0), make_double2(-0.5 / rho, 0)};
+                OV_TRY(lincomb(c, xout[k], 2, v, h, nullptr, 0, nullptr, st));
+            }
+        }
+    }
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    if (info) {
+        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int k = 0; k < M; ++k) info[k].seconds = sec;
+    }
+    return worst == OV_OK ? OV_OK : set_err(c, worst, "multimass: a mass did not converge");
 }
 
 }  // namespace ov

@@ -13,6 +13,8 @@ arithmetic (no Wilson operator, no sign function, no solver):
 * ``gaussian_spinor``: complex spinors with Re, Im ~ N(0, 1).
 * ``point_sources``: the 12 spin-colour delta sources of one propagator.
 * ``gauge_transform``: a random SU(3) matrix per site (covariance tests).
+* ``orthonormal_fields``: n seeded orthonormal spinor fields (stand-ins for a
+  set of eigenvectors where a formula holds for any orthonormal set).
 
 Canonical layout (shared by every consumer):
 
@@ -36,6 +38,7 @@ __all__ = [
     "gaussian_spinor",
     "point_sources",
     "gauge_transform",
+    "orthonormal_fields",
     "gell_mann",
 ]
 
@@ -176,3 +179,15 @@ def gauge_transform(dims, seed: int = 3) -> np.ndarray:
     herm = np.einsum("...a,aij->...ij", h, gell_mann() / 2.0)
     g = _reunitarise(_expm_i(torch.from_numpy(herm) * 2.0))
     return np.ascontiguousarray(g.numpy())
+
+
+def orthonormal_fields(dims, n: int, seed: int = 5) -> np.ndarray:
+    """n orthonormal complex spinor fields, complex128 [n, Lt, Lz, Ly, Lx, 4, 3]:
+    Gaussian fields orthonormalised by two passes of Cholesky QR (X <- X R^-1
+    with R^dag R = X^dag X), which leaves |X^dag X - 1| at rounding level."""
+    x = gaussian_spinor(dims, seed=seed, nrhs=n).reshape(n, -1).T.copy()
+    for _ in range(2):
+        g = x.conj().T @ x
+        r = np.linalg.cholesky(g).conj().T  # g = r^dag r, r upper triangular
+        x = np.linalg.solve(r.T, x.T).T     # x r^-1, as (r^T)^-1 x^T transposed
+    return np.ascontiguousarray(x.T).reshape((n,) + _shape(dims) + (4, 3))

@@ -106,6 +106,30 @@ def test_train_and_flexible_cg():
           f"FCG {fcg['iterations']} ({fcg['seconds']:.2f}s) fallback {fcg['fallback']}; true res {res:.2e}")
     assert res <= 1e-10
     assert loss < 1.0
+    # What the trained network gains over the method without it, recorded and asserted: a gain
+    # passes; no gain is the measured outcome on these inputs (the two-layer linear network learns a
+    # short-range approximation of the inverse that flexible CG cannot use better than deflated CG),
+    # reported as an expected failure with the figures, never silently passed.
+    if fcg["fallback"] or fcg["iterations"] >= plain["iterations"]:
+        pytest.xfail(f"learned preconditioner gives no gain: FCG {fcg['iterations']} iterations "
+                     f"(fallback {fcg['fallback']}) against {plain['iterations']} for plain deflated CG, "
+                     f"loss/pair {loss:.3f}")
+    assert fcg["seconds"] < plain["seconds"] * 1.5
+
+
+def test_zero_network_falls_back():
+    """A network with zero weights maps every residual to zero: flexible CG makes no progress, the
+    stall rule switches to plain deflated CG, and the solve still reaches the FP64 true residual."""
+    cf = setup((4, 4, 4, 8), 0.4, 7, 0.05, 60)
+    ctx = make_ctx(cf)
+    ctx.net_set_weights(np.zeros(4608, dtype=np.complex128))
+    b = synth.gaussian_spinor(cf["dims"], 13)
+    x = torch.empty_like(dev(b))
+    info = ctx.cg_solve(dev(b), x, mass=0.05, tol=1e-10, max_iter=3000, precond=1, inner_prec="f32")
+    assert info["fallback"] == 1
+    Ax = oracle.overlap_normal(cf["dims"], ABC, cf["U"], RHO, 0.05, cf["lmax"], cf["eps"], cf["c"], host(x),
+                               cf["ev"], cf["eta"])
+    assert rel(Ax, b) <= 1e-10
 
 
 def test_train_and_flexible_cg_chiral():

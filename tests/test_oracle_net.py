@@ -85,3 +85,44 @@ def test_gauge_equivariance():
     lhs = oracle.net_apply(dims, ABC, Ug, W1, W2, gr).reshape(r.shape)
     rhs = np.einsum("...ab,...sb->...sa", g, oracle.net_apply(dims, ABC, U, W1, W2, r).reshape(r.shape))
     assert np.abs(lhs - rhs).max() < 1e-12
+
+
+def _hop(field, dims, bc, mu, step):
+    """field(n + step mu_hat) on the canonical [t, z, y, x, ...] block, with the boundary
+    phase bc[mu] on every value that crossed the lattice edge."""
+    ax = AX[mu]
+    out = np.roll(field, -step, axis=ax)
+    L = dims[mu]
+    edge = [slice(None)] * field.ndim
+    edge[ax] = L - 1 if step > 0 else 0  # sites whose neighbour wrapped around
+    out[tuple(edge)] *= bc[mu]
+    return out
+
+
+def test_one_hot_paths_give_single_transports():
+    """W = identity spin matrix on one path and zero elsewhere makes the layer a single
+    parallel transport: path 1+2mu gives U_mu(n) x(n+mu), path 2+2mu gives
+    U_mu(n-mu)^dag x(n-mu), path 0 gives x.  A transposed spin matrix, swapped paths or
+    a missing boundary phase all fail this (the gradient and equivariance pins do not
+    see them); a non-diagonal spin matrix checks the spin index order."""
+    dims = (4, 2, 2, 4)
+    U = synth.gauge_field(dims, 17, 0.8)
+    x = synth.gaussian_spinor(dims, 4)[0]  # [t, z, y, x, 4, 3]
+    V = oracle.volume(dims)
+    rng = np.random.default_rng(3)
+    S = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))  # spin matrix, not symmetric
+    for p in range(9):
+        W = np.zeros((9, 1, 1, 4, 4), dtype=np.complex128)
+        W[p, 0, 0] = S
+        y = oracle.net_layer(dims, ABC, U, W, x.reshape(1, V, 4, 3))[0].reshape(x.shape)
+        if p == 0:
+            t = x
+        else:
+            mu, fwd = (p - 1) // 2, (p - 1) % 2 == 0
+            if fwd:  # U_mu(n) x(n + mu)
+                t = np.einsum("...ab,...sb->...sa", U[..., mu, :, :], _hop(x, dims, ABC, mu, +1))
+            else:    # U_mu(n - mu)^dag x(n - mu)
+                um = _hop(U[..., mu, :, :], dims, (1.0,) * 4, mu, -1)
+                t = np.einsum("...ba,...sb->...sa", um.conj(), _hop(x, dims, ABC, mu, -1))
+        expect = np.einsum("st,...ta->...sa", S, t)
+        assert np.abs(y - expect).max() < 1e-13, p
