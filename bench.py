@@ -170,11 +170,14 @@ def time_dslash(ctx, psi_dev, prec, nrhs, steps, warmup, torch):
     return ms, shape
 
 
-def dslash_config(world: int = 1) -> dict:
+def dslash_config(world: int = 1, prec: str = HEADLINE_PREC, nrhs: int = 1) -> dict:
     """The headline workload, the same for the GPU arm and the oracle (reference) arm."""
-    return {"workload": "wilson dslash D_w, 24^3x64 even/odd, FP64 storage and arithmetic (the paper's "
-                        "precision), 1 rhs, both parities per launch", "lattice": list(DIMS),
-            "gauge": "exp(0.5 iH) + 3 APE(0.6) steps", "parallelism": f"replicas x{world}",
+    if prec == HEADLINE_PREC and nrhs == 1:
+        what = "FP64 storage and arithmetic (the paper's precision), 1 rhs"
+    else:
+        what = f"{prec} storage, {nrhs} rhs (profiling run, not the headline)"
+    return {"workload": f"wilson dslash D_w, 24^3x64 even/odd, {what}, both parities per launch",
+            "lattice": list(DIMS), "gauge": "exp(0.5 iH) + 3 APE(0.6) steps", "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2: gauge 510 MB + spinors 2 x 170 MB per launch"}
 
 
@@ -220,15 +223,18 @@ def run_gpu(args):
            "how": "ov_measure_fma_peak: 8 independent FMA chains per thread, 8 x 256 threads per SM, "
                   "best of 5 launches (CUDA events), 2 flop per FMA"}
 
-    # ---- headline: FP64, 1 rhs (timed region bracketed by barrier + synchronize)
-    prec = HEADLINE_PREC
-    fi, fo = ctx.field(1, prec), ctx.field(1, prec)
+    # ---- headline: FP64, 1 rhs (timed region bracketed by barrier + synchronize); --prec / --nrhs
+    # select another launch of the same lattice for profiling runs
+    prec, nrhs = args.prec, args.nrhs
+    if nrhs > 1:
+        psi_dev = torch.from_numpy(make_inputs_rhs(nrhs)).cuda()
+    fi, fo = ctx.field(nrhs, prec), ctx.field(nrhs, prec)
     fi.load(psi_dev)
     if args.shape:
         bx, by, var = args.shape
-        ctx.set_dslash_shape(prec, 1, bx, by, var)
+        ctx.set_dslash_shape(prec, nrhs, bx, by, var)
     else:
-        bx, by, var = ctx.tune_dslash(prec, 1)
+        bx, by, var = ctx.tune_dslash(prec, nrhs)
     st = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.dslash_field(fi, fo, -RHO)
@@ -255,11 +261,13 @@ def run_gpu(args):
     time.sleep(0.3)
     clocks = clk.stop()
     ms = replica_time(e0.elapsed_time(e1) / (args.steps * reps), dist, "cuda")
-    bytes_launch = V * site_bytes(prec, 1)
+    bytes_launch = V * nrhs * site_bytes(prec, nrhs)
     gbs = bytes_launch / (ms * 1e-3) / 1e9
-    gflops = FLOP_SITE * V / (ms * 1e-3) / 1e9
+    gflops = FLOP_SITE * V * nrhs / (ms * 1e-3) / 1e9
     fi.close()
     fo.close()
+    if nrhs > 1:
+        psi_dev = torch.from_numpy(psi).cuda()
 
     # ---- variants (same lattice, other precisions and 12 rhs); the FP32 one is bound by HBM
     variants = {}
@@ -306,10 +314,11 @@ def run_gpu(args):
     if not args.quick and not args.no_prop and rank == 0:
         prop = propagator_record(args)
 
-    kern = kernel_name(prec, var)
+    kern = kernel_name(prec, var, nrhs)
+    fma_peak = fma["f64_gflops"] if prec == "f64" else fma["f32_gflops"]
     out = {
         "metric": METRIC,
-        "value": round(replica_throughput(FLOP_SITE * V / 1e9, world, ms), 2),
+        "value": round(replica_throughput(FLOP_SITE * V * nrhs / 1e9, world, ms), 2),
         "unit": "GFLOP/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -320,11 +329,13 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": prec,
         "data": "synthetic",
-        "config": dict(dslash_config(world), launch_shape=[bx, by], variant=var, launches_per_step=reps),
+        "config": dict(dslash_config(world, prec, nrhs), launch_shape=[bx, by], variant=var,
+                       launches_per_step=reps),
         "GBps": round(gbs * world, 1),
-        "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": fma["f64_gflops"], "unit": "GFLOP/s",
-                     "frac": round(gflops / fma["f64_gflops"], 4), "traffic": ncu_traffic(kern),
-                     "peak_kind": "measured: FP64 FMA throughput of this GPU (ov_measure_fma_peak, same run)",
+        "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": fma_peak, "unit": "GFLOP/s",
+                     "frac": round(gflops / fma_peak, 4), "traffic": ncu_traffic(kern),
+                     "peak_kind": f"measured: {prec if prec in ('f64', 'f32') else 'f32'} FMA throughput of this "
+                                  "GPU (ov_measure_fma_peak, same run)",
                      "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_nominal": round(gflops / FP64_NOMINAL_GFLOPS, 4),
                      "algorithmic_flops_per_launch": FLOP_SITE * V, "kernel": kern,
                      "hbm": {"achieved": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 4),
@@ -785,6 +796,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-prop", action="store_true", help="skip the propagator record of the default run")
+    ap.add_argument("--prec", default=HEADLINE_PREC, choices=list(REAL_BYTES),
+                    help="precision of the timed launch (profiling runs; the headline is f64)")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed launch (profiling runs)")
     ap.add_argument("--prop-dims", type=int, nargs=4, default=[8, 8, 8, 16])
     ap.add_argument("--prop-nev", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

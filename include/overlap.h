@@ -219,6 +219,18 @@ int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass
  * uses (option "proj_tc").  Returns OV_ETIMEOUT if a bounded wait inside the
  * tensor-core kernel gave up. */
 int ov_project_lowmodes(ov_ctx* ctx, int which, const ov_field* psi, int engine, double* out, void* stream);
+/* The low-mode update of Eq. 7 alone: out1_r = psi_r - sum_i v_i c[i][r] (the
+ * high-mode part psi_h) and, if out2 is not NULL, out2_r = gamma5 sum_i
+ * sign(val_i) c[i][r] v_i (gamma5 times the exact low-mode part of the sign),
+ * with the stored eigenvectors v_i of `which`.  coef: 2 * nev * nrhs doubles
+ * (re, im; [i][r]), host or device.  psi, out1 and out2: distinct fields of
+ * one precision and nrhs.  engine 0: CUDA cores in the fields' precision;
+ * engine 1: tensor cores (tcgen05, FP32 accumulation; bf16 rows for 16-bit
+ * fields, bf16 rows plus their bf16 remainders for FP32 fields; FP32 or
+ * 16-bit fields, nev <= 128, nrhs <= 16), which the FP32 and 16-bit overlap
+ * use (option "proj_tc").  Synchronises `stream`. */
+int ov_lowmode_update(ov_ctx* ctx, int which, const ov_field* psi, const double* coef, int engine, ov_field* out1,
+                      ov_field* out2, void* stream);
 /* Scalar products x_r^dag y_r of every right-hand side r (Sec. III: the
  * global scalar product), accumulated in FP64 whatever the storage precision
  * and reduced in a fixed order (bitwise reproducible).  out: 2 * nrhs doubles
@@ -286,10 +298,16 @@ int ov_measure_fma_peak(int prec, double* gflops, void* stream);
  *   "hi_prec" (OV_F64): precision of the accurate arithmetic in ov_cg_solve
  *                    (true residuals, solution accumulation) and of the
  *                    automatic ov_deflate operator: OV_F64 or OV_DF64;
- *   "proj_tc" (1):    16-bit overlap: compute eta^dag psi on the tensor cores
- *                    (0: on the CUDA cores);
+ *   "proj_tc" (1):    overlap: the low-mode projection on the tensor cores
+ *                    (eta^dag psi for 16-bit storage, the V c update for FP32
+ *                    and 16-bit storage; 0: everything on the CUDA cores);
  *   "net_sym" (1):    flexible CG applies the learned preconditioner as
  *                    (M + M^dag) / 2 (Hermitian) instead of M;
+ *   "clenshaw_f32" (1): 16-bit overlap (OV_F16S, OV_BF16S): the Clenshaw
+ *                    recurrence's work vectors are FP32 (the links stay 16-bit,
+ *                    the operator's input and output keep their 16-bit storage),
+ *                    which keeps the roundings of the n stored recurrence vectors
+ *                    out of the result; 0: every vector 16-bit;
  *   "adaptive_delta" (0): adaptive-precision CG (Sec. V, propagator paragraph:
  *                    adaptive CG).  > 0: the inner operator of ov_cg_solve and of
  *                    the shared recursion of ov_cg_solve_multimass uses the

@@ -73,6 +73,7 @@ _SIGS = {
     "ov_dslash_field": (_I, [_P, _P, _P, _D, _I, _P]),
     "ov_overlap_field": (_I, [_P, _P, _P, _D, _P]),
     "ov_field_dot": (_I, [_P, _P, _P, _P, _P]),
+    "ov_lowmode_update": (_I, [_P, _I, _P, _P, _I, _P, _P, _P]),
     "ov_project_lowmodes": (_I, [_P, _I, _P, _I, _P, _P]),
     "ov_field_dot_noalloc": (_I, [_P, _P, _P, _P]),
     "ov_device_bytes": (ctypes.c_longlong, [_P]),
@@ -349,6 +350,12 @@ class Context:
         out = np.empty(2 * n.value * psi.nrhs)
         self._check(self.lib.ov_project_lowmodes(self.h, int(which), psi.h, int(engine), _ptr(out), _stream(stream)))
         return out.view(np.complex128).reshape(n.value, psi.nrhs)
+
+    def lowmode_update(self, which, psi: Field, coef, out1: Field, out2: Field = None, engine=0, stream=None):
+        """ov_lowmode_update: out1 = psi - sum_i v_i c[i][r], out2 = gamma5 sum_i sign(val_i) c[i][r] v_i."""
+        cf = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
+        self._check(self.lib.ov_lowmode_update(self.h, int(which), psi.h, _ptr(cf), int(engine), out1.h,
+                                               out2.h if out2 is not None else None, _stream(stream)))
 
     def field_dot(self, x: Field, y: Field, stream=None):
         out = np.empty(2 * x.nrhs)

@@ -302,8 +302,10 @@ int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_
 // multiples of psi_h until a buffer is needed, so the launch count is 2n + 1.
 // Finally D(m) psi = (rho + m/2) psi + (rho - m/2) [D_w(P psi_h) / lmax + gamma5 sum_i sign(lam_i) c_i eta_i]
 // (gamma5 Q = D_w / lmax), in one more launch.
-static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out,
-                            cudaStream_t st, int poly = 0)
+// gprec: precision of the links (-1: that of the fields); dots16: the low-mode coefficients may come
+// from the bf16 tensor-core contraction (the operator's fields are 16-bit)
+static int overlap_core(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out,
+                        cudaStream_t st, int poly, int gprec, bool dots16)
 {
     // poly 1: the inner polynomial of the adaptive-precision CG (lower degree, same [eps, 1])
     const std::vector<double>& coef = poly ? c->coef_in : c->coef;
@@ -332,16 +334,22 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
         OV_TRY(ensure_partials(c, nparts * ncoef * sizeof(double2)));
         if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "overlap: nev * nrhs = %zu too large", ncoef);
         double2* dcoef = (double2*)c->dscal;
-        // 16-bit storage: c = eta^dag psi as a bf16 tensor-core GEMM; otherwise on the CUDA cores
-        const bool tc = c->proj_tc && (P == P_F16 || P == P_BF16) && E.nev <= 128 && 2 * R <= 256 &&
-                        (48LL * c->g.Vh) % 64 == 0;
-        if (tc) {
+        // tensor cores (tcgen05): c = eta^dag psi for 16-bit storage (bf16 operands), and the V c update
+        // for FP32 (bf16 rows plus their bf16 remainders) and 16-bit storage; FP64 and double-float stay on
+        // the CUDA cores
+        const bool tc_ok = c->proj_tc && E.nev <= 128 && R <= 16 && c->g.Vh % 8 == 0;
+        const bool tc_dots = tc_ok && (P == P_F16 || P == P_BF16 || dots16);
+        const bool tc_upd = tc_ok && (P == P_F16 || P == P_BF16 || P == P_F32);
+        if (tc_dots) {
             OV_TRY(proj_dots_tc(c, 0, in, dcoef, st));
         } else {
             OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
             OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
         }
-        OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));
+        if (tc_upd)
+            OV_TRY(proj_update_tc(c, 0, in, dcoef, E.d_sign, ph, w, st));
+        else
+            OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));
         src = ph;
     }
     const double alpha = 4.0 / (lam * lam * (1.0 - eps));
@@ -387,9 +395,9 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
         y[0] = src;
         sy[0] = psi_coef;
         // t = H_w b_{k+1} (unscaled), then b_k = f alpha hscale H_w t + sum_j sy_j y_j
-        OV_TRY(dslash_apply(c, *hin, t, aw, -0.5, 1, 0, 0, nullptr, nullptr, st));
+        OV_TRY(dslash_apply(c, *hin, t, aw, -0.5, 1, 0, 0, nullptr, nullptr, st, gprec));
         const double sc = f * alpha * hscale;
-        OV_TRY(dslash_apply(c, t, B[outbuf], sc * aw, -0.5 * sc, 1, 0, ny, y, sy, st));
+        OV_TRY(dslash_apply(c, t, B[outbuf], sc * aw, -0.5 * sc, 1, 0, ny, y, sy, st, gprec));
         b2 = b1;
         b1 = BRef{outbuf, 0.0};
     }
@@ -399,8 +407,28 @@ static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out
     const double psc = b1.buf >= 0 ? 1.0 : b1.g;
     FieldDesc y[2] = {in, defl ? w : in};
     double sy[2] = {rho + 0.5 * mass, rho - 0.5 * mass};
-    OV_TRY(dslash_apply(c, *pin, out, kk * psc * aw, -0.5 * kk * psc, 0, g5_out, defl ? 2 : 1, y, sy, st));
+    OV_TRY(dslash_apply(c, *pin, out, kk * psc * aw, -0.5 * kk * psc, 0, g5_out, defl ? 2 : 1, y, sy, st, gprec));
     return OV_OK;
+}
+
+// D(m) in (gamma5 D(m) in if g5_out).  16-bit fields (option "clenshaw_f32", the default): the
+// recurrence's work vectors are FP32 while the links stay 16-bit and the operator's input and output
+// keep their 16-bit storage.  A Clenshaw sum of degree n carries the roundings of its n stored b_k
+// through the remaining steps (the second-kind Chebyshev polynomials grow towards the ends of
+// [eps, 1]), so 16-bit b_k put the overlap above 1e-3 where the lowest undeflated mode sits at the
+// interval's edge; FP32 b_k leave the input, output and link roundings.  The kernel is bound by
+// latency and issue, not bytes, so the FP32 work vectors cost little time.
+static int overlap_apply_g5(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, double mass, int g5_out,
+                            cudaStream_t st, int poly = 0)
+{
+    const int P = in.prec;
+    if (!(c->clenshaw_f32 && (P == P_F16 || P == P_BF16))) return overlap_core(c, in, out, mass, g5_out, st, poly, -1, false);
+    FieldDesc i32, o32;
+    OV_TRY(ws_field(c, WS_MX0, P_F32, in.nrhs, &i32));
+    OV_TRY(ws_field(c, WS_MX1, P_F32, in.nrhs, &o32));
+    OV_TRY(convert(c, in, i32, st));
+    OV_TRY(overlap_core(c, i32, o32, mass, g5_out, st, poly, P, true));
+    return convert(c, o32, out, st);
 }
 
 void eig_clear(ov_ctx* c, EigSet& E)
@@ -408,9 +436,12 @@ void eig_clear(ov_ctx* c, EigSet& E)
     for (auto& f : E.vec) field_free(c, &f);
     if (E.d_sign) dev_free(c, E.d_sign, sizeof(double) * E.nev);
     if (E.tc_rows) dev_free(c, E.tc_rows, E.tc_bytes);
+    if (E.tc_lo) dev_free(c, E.tc_lo, E.tc_lo_bytes);
     E.d_sign = nullptr;
     E.tc_rows = nullptr;
     E.tc_bytes = 0;
+    E.tc_lo = nullptr;
+    E.tc_lo_bytes = 0;
     E.nev = 0;
     E.vals.clear();
 }
@@ -699,6 +730,7 @@ int ov_destroy(ov_ctx* c)
     for (auto& kv : c->ws) field_free(c, &kv.second);
     if (c->partials) dev_free(c, c->partials, c->partials_bytes);
     if (c->tc_b) dev_free(c, c->tc_b, c->tc_b_bytes);
+    if (c->tc_cb) dev_free(c, c->tc_cb, c->tc_cb_bytes);
     if (c->tc_err) dev_free(c, c->tc_err, sizeof(int));
     for (int i = 0; i < 2; ++i)
         if (c->stage[i]) dev_free(c, c->stage[i], c->stage_bytes[i]);
@@ -1105,6 +1137,39 @@ int ov_project_lowmodes(ov_ctx* c, int which, const ov_field* psi, int engine, d
     return OV_OK;
 }
 
+int ov_lowmode_update(ov_ctx* c, int which, const ov_field* psi, const double* coef, int engine, ov_field* out1,
+                      ov_field* out2, void* stream)
+{
+    if (!c || !psi || !coef || !out1) return c ? set_err(c, OV_EINVAL, "null pointer") : OV_EINVAL;
+    if (which != 0 && which != 1) return set_err(c, OV_EINVAL, "which = %d (0 or 1)", which);
+    EigSet& E = c->eig[which];
+    if (!E.nev) return set_err(c, OV_ESTATE, "no eigenpairs stored (which=%d)", which);
+    const FieldDesc& pd = psi->d;
+    for (const ov_field* o : {(const ov_field*)out1, (const ov_field*)out2})
+        if (o && (o->d.prec != pd.prec || o->d.nrhs != pd.nrhs))
+            return set_err(c, OV_EINVAL, "fields differ in precision or nrhs");
+    if (out1 == psi || out2 == psi || out1 == out2) return set_err(c, OV_EINVAL, "fields must differ");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ncoef = (size_t)E.nev * pd.nrhs;
+    if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "nev * nrhs = %zu too large", ncoef);
+    double2* dev = (double2*)c->dscal;
+    OV_CUDA(c, cudaMemcpyAsync(dev, coef, ncoef * sizeof(double2), cudaMemcpyDefault, st));
+    FieldDesc o2{};
+    if (out2) o2 = out2->d;
+    if (engine == 1) {
+        OV_TRY(proj_update_tc(c, which, pd, dev, E.d_sign, out1->d, o2, st));
+        OV_TRY(proj_tc_status(c, st));
+    } else if (engine == 0) {
+        FieldDesc eta;
+        OV_TRY(eig_vectors(c, which, pd.prec, st, &eta));
+        OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dev, E.d_sign, pd, out1->d, o2, st));
+    } else {
+        return set_err(c, OV_EINVAL, "engine = %d (0 CUDA cores, 1 tensor cores)", engine);
+    }
+    OV_CUDA(c, cudaStreamSynchronize(st));
+    return OV_OK;
+}
+
 long long ov_device_bytes(const ov_ctx* c) { return c ? c->bytes : -1; }
 
 long long ov_dslash_count(const ov_ctx* c) { return c ? c->dslash_launches : -1; }
@@ -1137,6 +1202,9 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
         c->net_sym = value != 0;
     } else if (n == "chiral") {
         c->chiral = value != 0;
+    } else if (n == "clenshaw_f32") {
+        graphs_clear(c);
+        c->clenshaw_f32 = value != 0;
     } else if (n == "adaptive_delta") {
         if (!(value >= 0 && value < 1)) return set_err(c, OV_EINVAL, "adaptive_delta must lie in [0, 1)");
         graphs_clear(c);
@@ -1170,6 +1238,7 @@ int ov_get_option(const ov_ctx* c, const char* name, double* value)
     else if (n == "hi_prec") *value = c->hi_prec;
     else if (n == "wait_polls") *value = (double)c->wait_polls;
     else if (n == "adaptive_delta") *value = c->adaptive_delta;
+    else if (n == "clenshaw_f32") *value = c->clenshaw_f32;
     else if (n == "adaptive_degree") *value = c->degree_in;
     else return OV_EINVAL;
     return OV_OK;

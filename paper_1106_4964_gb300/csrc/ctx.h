@@ -34,7 +34,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
-    WS_CG_BH, WS_CG_XH,
+    WS_CG_BH, WS_CG_XH, WS_TC0, WS_TC1, WS_MX0, WS_MX1,
     WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
@@ -46,6 +46,8 @@ struct EigSet {
     double* d_sign = nullptr;   // device sign(lam_i) (which = 0)
     void* tc_rows = nullptr;    // bf16 rows of the tensor-core projection [nev][24V]
     size_t tc_bytes = 0;
+    void* tc_lo = nullptr;      // bf16 remainders of the FP32 copy (FP32-class tensor-core operand)
+    size_t tc_lo_bytes = 0;
 };
 
 struct NetState;  // learned preconditioner (net.cu)
@@ -108,11 +110,14 @@ struct ov_ctx {
     int net_sym = 1;              // learned preconditioner applied as (M + M^dag) / 2
     int hi_prec = ov::P_F64;      // accurate arithmetic of the solvers: P_F64 or P_DF64
     int chiral = 0;               // ov_cg_solve: inner operator restricted to one chiral sector
+    int clenshaw_f32 = 1;         // 16-bit overlap: FP32 work vectors in the Clenshaw recurrence
     long long wait_polls = ov::DSLASH_WAIT_POLLS;  // first bounded wait of the bulk-copy dslash (option "wait_polls")
 
     // tensor-core projection buffers (proj_tc.cu)
     void* tc_b = nullptr;
     size_t tc_b_bytes = 0;
+    void* tc_cb = nullptr;  // bf16 coefficient operand of the tensor-core V c update
+    size_t tc_cb_bytes = 0;
     int* tc_err = nullptr;
 
     std::string err;
@@ -187,5 +192,8 @@ void eig_clear(ov_ctx* c, EigSet& E);
 // tensor-core projection (proj_tc.cu): c[i][r] = eta_i^dag psi_r, device double2 [nev][R]
 int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st);
 int proj_tc_status(ov_ctx* c, cudaStream_t st);
+// out1 = psi - sum_i eta_i c_i, out2 = gamma5 sum_i s_i c_i eta_i on the tensor cores (FP32 / 16-bit fields)
+int proj_update_tc(ov_ctx* c, int which, const FieldDesc& psi, const double2* dcoef, const double* dsign,
+                   const FieldDesc& out1, const FieldDesc& out2, cudaStream_t st);
 
 }  // namespace ov

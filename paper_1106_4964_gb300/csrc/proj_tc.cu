@@ -254,6 +254,17 @@ __global__ void build_b_kernel(const float4* __restrict__ x, int n4, int nrhs, _
     b2[1] = __floats2bfloat162_rn(v.w, -v.z);
 }
 
+// the bf16 remainder x - bf16(x) of each FP32 value
+__global__ void to_bf16_lo_kernel(const float4* __restrict__ x, long long n4, __nv_bfloat16* y)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n4) return;
+    const float4 v = x[q];
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[4 * q + j] = __float2bfloat16_rn(e[j] - __bfloat162float(__float2bfloat16_rn(e[j])));
+}
+
 __global__ void to_bf16_kernel(const float4* __restrict__ x, long long n4, __nv_bfloat16* y)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,6 +303,260 @@ bool make_map(CUtensorMap* m, const void* ptr, long long K, int rows, int box_ro
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------------------
+// V c on the tensor cores (Eq. 7: psi_h = psi - sum_i eta_i c_i and the exact low-mode
+// part sum_i sign(lam_i) c_i eta_i).  As a real GEMM over the eigenvector index i:
+//   P[k][col] = sum_i eta_i[k] B[i][col],  k = a real position of the field (FP32 internal order),
+// with four B columns per right-hand side r, (c_re, c_im, s c_re, s c_im) (s = sign(lam_i)), each
+// split into a bf16 high part and a bf16 remainder (8 columns), so the coefficients lose nothing.
+// Real position k = 2m holds Re eta(m), k = 2m + 1 holds Im eta(m); the complex product is
+// assembled in the epilogue from the row and its neighbour (TMEM lanes k and k ^ 1):
+//   corr_re(m) = X(2m) - Y(2m+1),  corr_im(m) = Y(2m) + X(2m+1),  X = P[.][c_re], Y = P[.][c_im].
+// A = the eigenvector rows (bf16, [nev][48 Vh]) read as an MN-major operand: a tile is 128
+// consecutive real positions (two 64-element swizzle atoms, LBO apart) by the eigenvector index
+// (8-row groups 1024 bytes apart), loaded by TMA straight from the row-major copy; rows i >= nev
+// are zero-filled by the TMA bounds and cost no traffic.  nsplit = 2 adds the rows of the bf16
+// remainder eta - bf16(eta) into the same accumulator (FP32-class eigenvectors at 4 bytes per real).
+// Persistent, warp-specialised: warp 0 issues the TMA loads into a ring of stages, warp 1 issues
+// tcgen05.mma into one of two TMEM accumulators, warps 2-5 (one per TMEM lane quarter) drain the
+// other accumulator and write the outputs, so loads, MMAs and stores overlap.
+constexpr int UP_M = 128;
+constexpr int UP_THREADS = 192;
+
+struct UpArgs {
+    long long ntiles;      // 48 Vh / 128
+    int kpadA;             // A box rows: nev rounded up to 16
+    int kchunksB;          // 64-element K chunks of B
+    int npad;              // B rows = accumulator columns (8 per rhs, padded to 16)
+    int nsplit;            // 1: eta rows; 2: also the remainder rows
+    int stages;
+    int R;
+    int Vh;
+    int mode;              // 0: FP32 fields, out1 = psi - corr, out2 = gamma5 w; 1: out1 = corr, out2 = gamma5 w
+    const float* psi;      // FP32 field (mode 0)
+    float* out1;
+    float* out2;           // may be null
+    int* err;
+};
+
+// MN-major operand descriptor, 128-byte swizzle: atoms of 64 MN elements x 8 K rows (1024 bytes),
+// K groups SBO = 1024 bytes apart, the second MN atom LBO bytes further
+__device__ __forceinline__ uint64_t smem_desc_mn(const void* p, uint32_t lbo)
+{
+    const uint64_t addr = smem_u32(p);
+    return ((addr >> 4) & 0x3FFFull) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) | ((1024ull >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+__global__ void __launch_bounds__(UP_THREADS, 1)
+    proj_update_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+                          const __grid_constant__ CUtensorMap tmB, UpArgs P)
+{
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ __align__(8) uint64_t full_bar[4], empty_bar[4], tfull[2], tempty[2], bbar, fin_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ long long consumed;  // tiles whose stage the MMA thread has taken (for the producer's drain)
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    const int S = P.stages;
+    const uint32_t half_bytes = (uint32_t)P.kpadA * 128;             // one MN atom column of A
+    const uint32_t stage_bytes = (uint32_t)P.nsplit * 2 * half_bytes;
+    uint8_t* bsm = base + (size_t)S * stage_bytes;
+    const uint32_t bchunk = (uint32_t)P.npad * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = 2 * P.npad;
+    const int tcols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : 256));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(&bbar, 1);
+        mbar_init(&fin_bar, 1);
+        abort_flag = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const long long my_tiles = P.ntiles > blockIdx.x ? (P.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 0 && lane == 0) {
+        // producer: B once, then the A tiles through the ring
+        mbar_expect_tx(&bbar, (uint32_t)P.kchunksB * bchunk);
+        for (int c = 0; c < P.kchunksB; ++c) tma_load_2d(bsm + (size_t)c * bchunk, &tmB, c * 64, 0, &bbar);
+        long long it = 0;
+        for (; it < my_tiles; ++it) {
+            const int s = (int)(it % S);
+            const uint32_t ph = (uint32_t)((it / S) & 1);
+            if (it >= S && !mbar_wait(&empty_bar[s], ph ^ 1)) {
+                atomicExch(P.err, 11);
+                abort_flag = 1;
+                break;
+            }
+            if (*(volatile int*)&abort_flag) break;
+            const long long tile = blockIdx.x + it * gridDim.x;
+            uint8_t* st = base + (size_t)s * stage_bytes;
+            mbar_expect_tx(&full_bar[s], stage_bytes);
+            const int x0 = (int)(tile * UP_M);
+            tma_load_2d(st, &tmA, x0, 0, &full_bar[s]);
+            tma_load_2d(st + half_bytes, &tmA, x0 + 64, 0, &full_bar[s]);
+            if (P.nsplit == 2) {
+                tma_load_2d(st + 2 * half_bytes, &tmAlo, x0, 0, &full_bar[s]);
+                tma_load_2d(st + 3 * half_bytes, &tmAlo, x0 + 64, 0, &full_bar[s]);
+            }
+        }
+        // drain: no block leaves with bulk copies in flight (the bounded waits of the stages that were
+        // issued and never taken by the MMA thread)
+        __threadfence_block();
+        for (long long t = *(volatile long long*)&consumed; t < it; ++t)
+            mbar_wait(&full_bar[t % S], (uint32_t)((t / S) & 1));
+        mbar_wait(&bbar, 0);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(UP_M, P.npad) | (1u << 15);  // A MN-major
+        const int ksteps = P.kpadA / 16;
+        bool ok = mbar_wait(&bbar, 0);
+        if (!ok) {
+            atomicExch(P.err, 12);
+            abort_flag = 1;
+        }
+        for (long long it = 0; ok && it < my_tiles; ++it) {
+            const int s = (int)(it % S);
+            const int a = (int)(it & 1);
+            if (*(volatile int*)&abort_flag) break;
+            if (!mbar_wait(&full_bar[s], (uint32_t)((it / S) & 1))) {
+                atomicExch(P.err, 13);
+                abort_flag = 1;
+                break;
+            }
+            consumed = it + 1;
+            if (it >= 2 && !mbar_wait(&tempty[a], (uint32_t)(((it >> 1) & 1) ^ 1))) {
+                atomicExch(P.err, 14);
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t* st = base + (size_t)s * stage_bytes;
+            const uint32_t d = tmem + (uint32_t)(a * P.npad);
+            for (int sp = 0; sp < P.nsplit; ++sp)
+                for (int j = 0; j < ksteps; ++j) {
+                    const uint64_t ad = smem_desc_mn(st + (size_t)sp * 2 * half_bytes + (size_t)j * 2048, half_bytes);
+                    const uint64_t bd = smem_desc(bsm + (size_t)(j >> 2) * bchunk + (j & 3) * 32);
+                    mma_bf16(d, ad, bd, idesc, (sp > 0 || j > 0) ? 1u : 0u);
+                }
+            mma_commit(&empty_bar[s]);  // the stage is free once these MMAs have read it
+            mma_commit(&tfull[a]);      // the accumulator is ready for the epilogue
+        }
+        mma_commit(&fin_bar);  // arrives when every MMA issued by this thread has completed
+        if (!mbar_wait(&fin_bar, 0)) atomicExch(P.err, 15);
+    } else if (warp >= 2) {
+        // epilogue: TMEM lane quarter q of the accumulator, row = q * 32 + lane
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const long long rhs_reals = 48LL * P.Vh;
+        const long long par_reals = 24LL * P.Vh;
+        const long long lo_chunk = 12LL * P.Vh;  // chunks 3..5 of a parity (spins 2, 3) start here
+        for (long long it = 0; it < my_tiles; ++it) {
+            const int a = (int)(it & 1);
+            if (*(volatile int*)&abort_flag) break;
+            if (!mbar_wait(&tfull[a], (uint32_t)((it >> 1) & 1))) {
+                if (lane == 0) atomicExch(P.err, 16);
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long tile = blockIdx.x + it * gridDim.x;
+            const long long k = tile * UP_M + row;
+            const bool lower = (k % par_reals) >= lo_chunk;  // gamma5 = -1 on spins 2, 3
+            const float g5 = lower ? -1.f : 1.f;
+            const float sg = (lane & 1) ? 1.f : -1.f;
+            for (int c0 = 0; c0 < P.npad; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * P.npad + c0), v);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = (c0 >> 3) + h;  // 8 columns per rhs
+                    const float X = v[8 * h + 0] + v[8 * h + 4], Y = v[8 * h + 1] + v[8 * h + 5];
+                    const float XW = v[8 * h + 2] + v[8 * h + 6], YW = v[8 * h + 3] + v[8 * h + 7];
+                    const float Yp = __shfl_xor_sync(0xffffffffu, Y, 1);
+                    const float YWp = __shfl_xor_sync(0xffffffffu, YW, 1);
+                    if (r < P.R) {
+                        const float corr = X + sg * Yp, w = XW + sg * YWp;
+                        const long long idx = (long long)r * rhs_reals + k;
+                        P.out1[idx] = P.mode == 0 ? P.psi[idx] - corr : corr;
+                        if (P.out2) P.out2[idx] = g5 * w;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[a])) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// B[n][k] (bf16, [npad][kchunks * 64]): n = 8 r + j, k = eigenvector index; j = 0..3: high parts of
+// (c_re, c_im, s c_re, s c_im), j = 4..7: their bf16 remainders; zero outside (r < R, k < nev)
+__global__ void build_coef_b_kernel(const double2* __restrict__ cf, const double* __restrict__ sg, int nev, int R,
+                                    int npad, int kp, __nv_bfloat16* B)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (k >= kp || n >= npad) return;
+    float v = 0.f;
+    const int r = n >> 3, j = n & 7;
+    if (r < R && k < nev) {
+        const double2 c = cf[(size_t)k * R + r];
+        const double s = sg ? sg[k] : 0.0;
+        const int t = j & 3;
+        const double x = t == 0 ? c.x : (t == 1 ? c.y : (t == 2 ? s * c.x : s * c.y));
+        const float hi = __bfloat162float(__float2bfloat16_rn((float)x));
+        v = j < 4 ? hi : (float)(x - (double)hi);
+    }
+    B[(size_t)n * kp + k] = __float2bfloat16_rn(v);
+}
+
+// out1 = psi - corr and out2 = w (already gamma5-signed), corr and w FP32 fields, psi and the
+// outputs in a 16-bit storage precision (per-site scale recomputed on store)
+template <int P>
+__global__ void proj_combine_kernel(Geom g, FieldDesc psi, const float* corr, const float* w, FieldDesc out1,
+                                    FieldDesc out2)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (idx >= 2 * g.Vh) return;
+    const int p = idx >= g.Vh, s = idx - p * g.Vh;
+    const size_t rp = (size_t)r * 2 + p;
+    constexpr size_t CH = nchunk_dev<P>() * 16;
+    float a[24], c[24];
+    load_spinor<P, float>(psi.data + rp * CH * g.Vh, psi.norm ? psi.norm + rp * g.Vh : nullptr, g.Vh, s, a);
+    load_spinor<P_F32, float>(reinterpret_cast<const char*>(corr) + rp * 96 * g.Vh, nullptr, g.Vh, s, c);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) a[i] -= c[i];
+    store_spinor<P, float>(out1.data + rp * CH * g.Vh, out1.norm ? out1.norm + rp * g.Vh : nullptr, g.Vh, s, a);
+    if (w) {
+        load_spinor<P_F32, float>(reinterpret_cast<const char*>(w) + rp * 96 * g.Vh, nullptr, g.Vh, s, c);
+        store_spinor<P, float>(out2.data + rp * CH * g.Vh, out2.norm ? out2.norm + rp * g.Vh : nullptr, g.Vh, s, c);
+    }
+}
+
 }  // namespace
 
 // bf16 copy of the eigenvectors (rows of A), built once from the FP32 copy
@@ -311,6 +576,127 @@ int eig_bf16_rows(ov_ctx* c, int which, cudaStream_t st, const void** out)
         OV_CUDA(c, cudaGetLastError());
     }
     *out = E.tc_rows;
+    return OV_OK;
+}
+
+int eig_bf16_lo_rows(ov_ctx* c, int which, cudaStream_t st, const void** out)
+{
+    EigSet& E = c->eig[which];
+    const void* hi = nullptr;
+    OV_TRY(eig_bf16_rows(c, which, st, &hi));
+    if (!E.tc_lo) {
+        FieldDesc f32;
+        OV_TRY(eig_vectors(c, which, P_F32, st, &f32));
+        const long long K = 48LL * c->g.Vh;
+        OV_TRY(dev_alloc(c, &E.tc_lo, (size_t)E.nev * K * 2));
+        E.tc_lo_bytes = (size_t)E.nev * K * 2;
+        // remainder of the FP32 copy: hi + lo carries 16 significand bits of the FP32 value, which is what
+        // the FP32 arithmetic of the operator resolves
+        const long long n4 = (long long)E.nev * K / 4;
+        to_bf16_lo_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>((const float4*)f32.data, n4,
+                                                                        (__nv_bfloat16*)E.tc_lo);
+        OV_CUDA(c, cudaGetLastError());
+    }
+    *out = E.tc_lo;
+    return OV_OK;
+}
+
+// out1_r = psi_r - sum_i eta_i c[i][r], out2_r = gamma5 sum_i s_i c[i][r] eta_i (out2.data may be null)
+// on the tensor cores; c: device double2 [nev][R], s: device sign(lam_i) (may be null).  16-bit
+// storage reads the bf16 rows; FP32 storage adds the bf16 remainder rows.
+int proj_update_tc(ov_ctx* c, int which, const FieldDesc& psi, const double2* dcoef, const double* dsign,
+                   const FieldDesc& out1, const FieldDesc& out2, cudaStream_t st)
+{
+    EigSet& E = c->eig[which];
+    const int nev = E.nev, R = psi.nrhs;
+    if (nev < 1 || nev > 128 || R > 16 || c->g.Vh % 8)
+        return set_err(c, OV_EINVAL, "tensor-core update: nev %d (1..128), nrhs %d (<= 16), Vh %% 8", nev, R);
+    const int P = psi.prec;
+    if (P != P_F32 && P != P_F16 && P != P_BF16)
+        return set_err(c, OV_EINVAL, "tensor-core update: FP32 or 16-bit storage only");
+    const int nsplit = P == P_F32 ? 2 : 1;
+    const void* A = nullptr;
+    const void* Alo = nullptr;
+    OV_TRY(eig_bf16_rows(c, which, st, &A));
+    if (nsplit == 2) OV_TRY(eig_bf16_lo_rows(c, which, st, &Alo));
+    const long long K = 48LL * c->g.Vh;
+    const int npad = ((8 * R + 15) / 16) * 16;
+    const int kpadA = ((nev + 15) / 16) * 16;
+    const int kchunksB = (nev + 63) / 64;
+    const int kpB = kchunksB * 64;
+    const size_t bbytes_g = (size_t)npad * kpB * 2;
+    if (c->tc_cb_bytes < bbytes_g) {
+        if (c->tc_cb) {
+            cudaDeviceSynchronize();
+            dev_free(c, c->tc_cb, c->tc_cb_bytes);
+        }
+        c->tc_cb = nullptr;
+        c->tc_cb_bytes = 0;
+        graphs_clear(c);
+        OV_TRY(dev_alloc(c, &c->tc_cb, bbytes_g));
+        c->tc_cb_bytes = bbytes_g;
+    }
+    build_coef_b_kernel<<<dim3((kpB + 127) / 128, npad), 128, 0, st>>>(dcoef, out2.data ? dsign : nullptr, nev, R,
+                                                                        npad, kpB, (__nv_bfloat16*)c->tc_cb);
+    OV_CUDA(c, cudaGetLastError());
+    CUtensorMap ma, malo, mb;
+    if (!make_map(&ma, A, K, nev, kpadA) || !make_map(&malo, nsplit == 2 ? Alo : A, K, nev, kpadA) ||
+        !make_map(&mb, c->tc_cb, kpB, npad, npad))
+        return set_err(c, OV_ECUDA, "cuTensorMapEncodeTiled failed");
+    const uint32_t stage_bytes = (uint32_t)nsplit * 2 * kpadA * 128;
+    const uint32_t bbytes = (uint32_t)kchunksB * npad * 128;
+    constexpr int kSmemMax = 227 * 1024;
+    const int stages = std::min(4, (int)((kSmemMax - 1024 - (int)bbytes) / (int)stage_bytes));
+    if (stages < 2) return set_err(c, OV_EINVAL, "tensor-core update: tiles do not fit in shared memory");
+    const size_t smem = (size_t)stages * stage_bytes + bbytes + 1024;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(proj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    OV_CUDA(c, attr);
+    if (!c->tc_err) {
+        void* p = nullptr;
+        OV_TRY(dev_alloc(c, &p, sizeof(int)));
+        c->tc_err = (int*)p;
+        OV_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), st));
+    }
+    UpArgs a;
+    memset(&a, 0, sizeof a);
+    a.ntiles = K / UP_M;
+    a.kpadA = kpadA;
+    a.kchunksB = kchunksB;
+    a.npad = npad;
+    a.nsplit = nsplit;
+    a.stages = stages;
+    a.R = R;
+    a.Vh = c->g.Vh;
+    a.err = c->tc_err;
+    FieldDesc corr{}, wf{};
+    if (P == P_F32) {
+        a.mode = 0;
+        a.psi = (const float*)psi.data;
+        a.out1 = (float*)out1.data;
+        a.out2 = out2.data ? (float*)out2.data : nullptr;
+    } else {
+        OV_TRY(ws_field(c, WS_TC0, P_F32, R, &corr));
+        if (out2.data) OV_TRY(ws_field(c, WS_TC1, P_F32, R, &wf));
+        a.mode = 1;
+        a.out1 = (float*)corr.data;
+        a.out2 = out2.data ? (float*)wf.data : nullptr;
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int grid = (int)std::min<long long>(a.ntiles, sms);
+    proj_update_tc_kernel<<<grid, UP_THREADS, smem, st>>>(ma, malo, mb, a);
+    OV_CUDA(c, cudaGetLastError());
+    if (P != P_F32) {
+        const dim3 g2((2 * c->g.Vh + 127) / 128, R);
+        if (P == P_F16)
+            proj_combine_kernel<P_F16><<<g2, 128, 0, st>>>(c->g, psi, (const float*)corr.data,
+                                                           out2.data ? (const float*)wf.data : nullptr, out1, out2);
+        else
+            proj_combine_kernel<P_BF16><<<g2, 128, 0, st>>>(c->g, psi, (const float*)corr.data,
+                                                            out2.data ? (const float*)wf.data : nullptr, out1, out2);
+        OV_CUDA(c, cudaGetLastError());
+    }
     return OV_OK;
 }
 

@@ -61,7 +61,7 @@ def test_overlap_graph_replay_bitwise(cfg1, prec, on_stream):
     assert ctx.dslash_count() - n0 == 3 * per_call  # replays account for their launches
     for o in outs:
         assert np.array_equal(o, eager)
-    tol = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3}[prec]
+    tol = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3}[prec]  # per overlap application
     for r in range(2):
         ref = oracle.overlap(cf["dims"], ABC, cf["U"], RHO, 0.0, cf["lmax"], cf["eps"], cf["c"], psi[r], cf["ev"],
                              cf["eta"])

@@ -93,14 +93,14 @@ def test_multimass_twelve_sources_8c4():
 
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
-    eps, n, lmax = 0.01, 100, 6.6
+    eps, n, lmax = 0.0005, 400, 6.6  # [eps, 1] covers this field's H_w spectrum (no H_w deflation)
     c = oracle.cheb_coeffs(eps, n)
     ctx = Context(dims, ABC)
     ctx.set_gauge(dev(U))
     ctx.set_sign_poly(RHO, eps, n, lmax)
     ctx.set_option("chiral", 1)
     ctx.tune_dslash("f32", 12)
-    ctx.deflate(1, 16, 1e-8)
+    ctx.deflate(1, 16, 1e-5)
     b = synth.point_sources(dims)
     masses = [0.05, 0.2]
     x = torch.empty((2,) + b.shape, dtype=torch.complex128, device="cuda")

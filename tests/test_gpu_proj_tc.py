@@ -82,3 +82,52 @@ def test_overlap_16bit_with_tensor_core_projection():
     print("16-bit overlap errors (tensor-core projection, prec):", errs)
     for (tc, prec), e in errs.items():
         assert e <= OTOL[prec], (tc, prec, e)
+
+
+# V c update on the tensor cores: bf16 rows (16-bit fields) lose ~2^-9 of |sum v c| per element;
+# FP32 fields add the bf16 remainder rows and keep ~2^-17 (coefficients are split the same way)
+UPD_TOL = {"f32": 5e-5, "f16": 1e-2, "bf16": 1.5e-2}
+
+
+@pytest.mark.parametrize("dims,nev,nrhs", [((8, 8, 8, 8), 20, 3), ((4, 4, 4, 4), 128, 1), ((8, 4, 4, 8), 37, 12),
+                                           ((16, 16, 16, 32), 100, 1)])
+def test_tensor_core_update(dims, nev, nrhs):
+    """out1 = psi - sum_i v_i c_i and out2 = gamma5 sum_i sign(val_i) c_i v_i (Eq. 7) by tcgen05 against
+    numpy in FP64 and against the CUDA-core engine, with coefficients as large as the field."""
+    from paper_1106_4964_gb300 import Context
+
+    V = oracle.volume(dims)
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(synth.unit_gauge(dims)))
+    vecs = synth.orthonormal_fields(dims, nev, seed=31).reshape(nev, -1)
+    rng = np.random.default_rng(32)
+    vals = rng.uniform(0.1, 1.0, nev) * rng.choice([-1.0, 1.0], nev)
+    ctx.set_eigenpairs(0, vals, dev(vecs))
+    psi = synth.gaussian_spinor(dims, 33, nrhs=nrhs).reshape(nrhs, -1)
+    scale = np.linalg.norm(psi[0]) / np.sqrt(nev)
+    coef = scale * (rng.standard_normal((nev, nrhs)) + 1j * rng.standard_normal((nev, nrhs)))
+    low = (vecs.T @ coef).T                                   # [nrhs, 12V]: sum_i v_i c_ir
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)
+    exp1 = psi - low
+    exp2 = g5 * (vecs.T @ (np.sign(vals)[:, None] * coef)).T
+    for prec in ("f32", "f16", "bf16"):
+        f, o1, o2 = ctx.field(nrhs, prec), ctx.field(nrhs, prec), ctx.field(nrhs, prec)
+        f.load(dev(psi.reshape((nrhs,) + synth.gaussian_spinor(dims, 1)[0].shape)))
+        got = {}
+        for engine in (1, 0):
+            ctx.lowmode_update(0, f, coef, o1, o2, engine=engine)
+            a, b = torch.empty_like(dev(psi)), torch.empty_like(dev(psi))
+            o1.store(a)
+            o2.store(b)
+            got[engine] = (host(a), host(b))
+        for r in range(nrhs):
+            e1 = rel(got[1][0][r], exp1[r])
+            e2 = rel(got[1][1][r], exp2[r])
+            assert e1 < UPD_TOL[prec] and e2 < UPD_TOL[prec], (prec, r, e1, e2)
+            # the CUDA-core engine in the same storage precision is no more accurate than that
+            assert rel(got[0][0][r], exp1[r]) < UPD_TOL[prec]
+        print(f"tensor-core update {dims} nev={nev} nrhs={nrhs} {prec}: worst rel err "
+              f"{max(rel(got[1][0][r], exp1[r]) for r in range(nrhs)):.2e} / "
+              f"{max(rel(got[1][1][r], exp2[r]) for r in range(nrhs)):.2e}")
+        for x in (f, o1, o2):
+            x.close()
