@@ -113,6 +113,22 @@ int ov_apply_normal(ov_ctx* ctx, const void* in, void* out, double mass, int nrh
  * library to estimate it (1.01 x the largest |eigenvalue| of H_w from 50
  * Lanczos steps on H_w^2; needs the gauge field).  0 < eps < 1, degree >= 0. */
 int ov_set_sign_poly(ov_ctx* ctx, double rho, double eps, int degree, double lambda_max);
+/* The rational alternative of Sec. V (Eq. 12): P(Q^2) psi_h = sum_i b_i
+ * (Q^2 + c_i)^-1 psi_h with Zolotarev's optimal coefficients for x^{-1/2} on
+ * [eps, 1] (npoles fractions, 1..64), the shifted inverses by one multi-shift
+ * CG on Q^2 = H_w^2 / lambda_max^2 to the relative residual of option
+ * "rational_tol" (1e-12; at least 1e-6 for FP32 and 16-bit fields), in the
+ * double-pass form (option "rational_pass" = 2, the default: the scalars of
+ * one pass, then a second pass that sums the solution; twice the dslash
+ * applications, three vector updates per iteration) or the single-pass form
+ * (1: 2 npoles shifted vectors).  The deflation of Eq. 7 and the overlap
+ * assembly are those of the polynomial.  Replaces the polynomial until the
+ * next ov_set_sign_poly.  Applications with this backend are not captured in
+ * CUDA graphs (the iteration tests convergence on the host). */
+int ov_set_sign_rational(ov_ctx* ctx, double rho, double eps, int npoles, double lambda_max);
+/* The rational backend's coefficients: *npoles, b[npoles], c[npoles] (may be
+ * NULL) and delta of Eq. 4; OV_ESTATE when the polynomial is in use. */
+int ov_get_sign_rational(const ov_ctx* ctx, int* npoles, double* b, double* c, double* delta);
 /* Current polynomial parameters (lambda_max after any estimate). */
 int ov_get_sign_poly(const ov_ctx* ctx, double* rho, double* eps, int* degree, double* lambda_max);
 
@@ -215,9 +231,11 @@ int ov_overlap_field(ov_ctx* ctx, const ov_field* in, ov_field* out, double mass
  * Eq. 9), out: 2 * nev * nrhs doubles (re, im; [i][r]), host or device.
  * engine 0: CUDA cores in the field's precision (FP64 for an FP64 field);
  * engine 1: tensor cores (tcgen05, bf16 operands, FP32 accumulation, FP64
- * sum of the split-K partials), nev <= 128, which is what the 16-bit overlap
- * uses (option "proj_tc").  Returns OV_ETIMEOUT if a bounded wait inside the
- * tensor-core kernel gave up. */
+ * sum of the split-K partials), nev <= 128; engine 2: the same with the bf16
+ * remainders of both operands added (eta_hi psi_hi + eta_hi psi_lo +
+ * eta_lo psi_hi: about 16 significand bits per product, FP32-class), which is
+ * what the FP32 and 16-bit overlap use (option "proj_tc").  Returns
+ * OV_ETIMEOUT if a bounded wait inside the tensor-core kernel gave up. */
 int ov_project_lowmodes(ov_ctx* ctx, int which, const ov_field* psi, int engine, double* out, void* stream);
 /* The low-mode update of Eq. 7 alone: out1_r = psi_r - sum_i v_i c[i][r] (the
  * high-mode part psi_h) and, if out2 is not NULL, out2_r = gamma5 sum_i
@@ -248,7 +266,11 @@ int ov_field_dot(ov_ctx* ctx, const ov_field* x, const ov_field* y, double* out,
  * All calls share the array and every call overwrites it completely, so
  * calls that overlap on the GPU (other streams, other threads) race: order
  * them.  The current device must be the fields' device.  out: 2 * nrhs
- * doubles, host or device.  Errors are returned as status codes only
+ * doubles, host or device; a host out makes the call copy the result and
+ * synchronise `stream`, which a stream being captured does not allow, so
+ * while capturing pass a device out.  The looked-up address belongs to the
+ * device's primary context: after cudaDeviceReset this entry point must not
+ * be called again in the process.  Errors are returned as status codes only
  * (ov_last_error is not updated, since setting its text could allocate). */
 int ov_field_dot_noalloc(const ov_field* x, const ov_field* y, double* out, void* stream);
 
@@ -303,6 +325,9 @@ int ov_measure_fma_peak(int prec, double* gflops, void* stream);
  *                    and 16-bit storage; 0: everything on the CUDA cores);
  *   "net_sym" (1):    flexible CG applies the learned preconditioner as
  *                    (M + M^dag) / 2 (Hermitian) instead of M;
+ *   "rational_pass" (2), "rational_tol" (1e-12): the rational sign
+ *                    (ov_set_sign_rational); "rational_iterations" (read only,
+ *                    ov_get_option): CG iterations of its last application;
  *   "clenshaw_f32" (1): 16-bit overlap (OV_F16S, OV_BF16S): the Clenshaw
  *                    recurrence's work vectors are FP32 (the links stay 16-bit,
  *                    the operator's input and output keep their 16-bit storage),

@@ -21,6 +21,12 @@ Functions and what pins each one (tests/test_oracle_*.py):
                               Ginsparg-Wilson relation, spectrum on the circle
                               |d - rho| = rho, D^dag D = rho (D + D^dag).
 ``overlap_normal`` / ``cg``   Eq. (9).  Dense linear solve on 2^4; true residual.
+``multimass_cg``              Sec. II.  Dense solves of every mass; single-mass CG.
+``ellipk`` / ``jacobi``       scipy.special's independent K(m) and ellipj.
+``zolotarev``                 Eq. (12).  Closed form at n = 1; equioscillation of
+                              the error with 2n + 1 extremes of equal size.
+``sign_rational``             Eqs. (7), (12).  Dense eigendecomposition sign on
+                              2^4; sign^2 = 1; agreement with the polynomial sign.
 ``net_layer`` / ``_grad``     No paper counterpart.  Central finite differences
                               and gauge equivariance.
 ============================  =====================================================
@@ -169,6 +175,66 @@ def _defl(evals, evecs, V):
     evecs = np.ascontiguousarray(evecs, dtype=np.complex128)
     assert evecs.size == len(evals) * 12 * V
     return len(evals), evals, evecs
+
+
+def ellipk(m: float) -> float:
+    """Complete elliptic integral K(m), parameter m = k^2 (AGM)."""
+    f = lib().or_ellipk
+    f.restype = ctypes.c_double
+    return f(ctypes.c_double(m))
+
+
+def jacobi(u: float, m: float):
+    """(sn, cn, dn)(u | m) by the descending AGM."""
+    sn, cn, dn = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_jacobi(ctypes.c_double(u), ctypes.c_double(m), ctypes.byref(sn), ctypes.byref(cn), ctypes.byref(dn))
+    return sn.value, cn.value, dn.value
+
+
+def zolotarev(eps: float, n: int):
+    """Zolotarev's optimal P(x) = sum_i b_i / (x + c_i) ~ x^{-1/2} on [eps, 1] (Eq. 12).
+    Returns (b, c, delta)."""
+    b, c = np.empty(n), np.empty(n)
+    f = lib().or_zolotarev
+    f.restype = ctypes.c_double
+    d = f(ctypes.c_double(eps), ctypes.c_int(n), _ptr(b), _ptr(c))
+    return b, c, d
+
+
+def rational_eval(b, c, x):
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    f = lib().or_rational_eval
+    f.restype = ctypes.c_double
+    return np.array([f(_ptr(b), _ptr(c), ctypes.c_int(len(b)), ctypes.c_double(v)) for v in np.atleast_1d(x)])
+
+
+def sign_rational(dims, bc, U, mw, lmax, b, c, x, tol=1e-14, evals=None, evecs=None):
+    """sign(H_w(mw)) x by Eq. (7) with the rational P of Eq. (12), shifted inverses by multi-shift CG."""
+    V = volume(dims)
+    x = _field(x, V)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    nev, lam, eta = _defl(evals, evecs, V)
+    out = np.empty_like(x)
+    lib().or_sign_rational(_dims(dims), _bc(bc), _ptr(_gauge(U, V)), ctypes.c_double(mw), ctypes.c_double(lmax),
+                           ctypes.c_int(len(b)), _ptr(b), _ptr(c), ctypes.c_double(tol), ctypes.c_int(nev), _ptr(lam),
+                           _ptr(eta), _ptr(x), _ptr(out))
+    return out
+
+
+def overlap_rational(dims, bc, U, rho, mass, lmax, b, c, x, tol=1e-14, evals=None, evecs=None):
+    """D(m) x with the rational sign (Eqs. 3, 8, 12)."""
+    V = volume(dims)
+    x = _field(x, V)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    nev, lam, eta = _defl(evals, evecs, V)
+    out = np.empty_like(x)
+    lib().or_overlap_rational(_dims(dims), _bc(bc), _ptr(_gauge(U, V)), ctypes.c_double(rho), ctypes.c_double(mass),
+                              ctypes.c_double(lmax), ctypes.c_int(len(b)), _ptr(b), _ptr(c), ctypes.c_double(tol),
+                              ctypes.c_int(nev), _ptr(lam), _ptr(eta), _ptr(x), _ptr(out))
+    return out
 
 
 def sign(dims, bc, U, mw, lmax, eps, coeffs, x, evals=None, evecs=None):

@@ -305,6 +305,11 @@ typedef struct {
     int nev;
     const double *lam; /* eigenvalues of H_w (signed) */
     const cplx *eta;   /* eigenvectors [nev][12V], orthonormal */
+    /* rational form of Eq. (12) instead of the polynomial when npoles > 0:
+       P(Q^2) psi_h = sum_i rb_i (Q^2 + rc_i)^-1 psi_h, solved by multi-shift CG to rtol */
+    int npoles;
+    const double *rb, *rc;
+    double rtol;
 } sign_args;
 
 /* out = Y in, with Y = (2 Q^2 - (1+eps)) / (1-eps), Q = H_w / lmax */
@@ -318,6 +323,8 @@ static void apply_Y(const sign_args *a, const cplx *in, cplx *out, cplx *tmp)
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; ++i) out[i] = s * out[i] - t * in[i];
 }
+
+static void rational_apply(const sign_args *a, const cplx *ph, cplx *pp);
 
 /* sign(H_w) in ~ sum_i sign(lam_i) (eta_i^dag in) eta_i + Q P(Q^2) (1 - P_l) in   (Eq. 7) */
 static void sign_apply(const sign_args *a, const cplx *in, cplx *out)
@@ -338,6 +345,11 @@ static void sign_apply(const sign_args *a, const cplx *in, cplx *out)
         for (long k = 0; k < N; ++k) ph[k] -= proj[i] * e[k];
     }
 
+    cplx *pp = y; /* P(Q^2) psi_h */
+    if (a->npoles > 0) {
+        rational_apply(a, ph, pp); /* Eq. (12) */
+        goto outer;
+    }
     /* Clenshaw: b_k = c_k psi_h + 2 Y b_{k+1} - b_{k+2}, k = n..1;
        P psi_h = c_0 psi_h + Y b_1 - b_2                            (Sec. V) */
     for (long k = 0; k < N; ++k) b1[k] = a->c[a->n] * ph[k]; /* b_n (b_{n+1} = 0) */
@@ -349,13 +361,13 @@ static void sign_apply(const sign_args *a, const cplx *in, cplx *out)
             b1[i] = b0;
         }
     }
-    cplx *pp = y; /* P(Q^2) psi_h */
     if (a->n >= 1) {
         apply_Y(a, b1, y, tmp);
         for (long i = 0; i < N; ++i) pp[i] = a->c[0] * ph[i] + y[i] - b2[i];
     } else {
         for (long i = 0; i < N; ++i) pp[i] = a->c[0] * ph[i];
     }
+outer:
     /* Q P(Q^2) psi_h */
     or_hw(a->d, a->bc, a->U, a->mw, pp, out);
     for (long i = 0; i < N; ++i) out[i] /= a->lmax;
@@ -381,6 +393,242 @@ void or_sign(const int *d, const double *bc, const cplx *U, double mw, double lm
     init_gamma();
     sign_args a = {d, bc, U, mw, lmax, eps, n, c, nev, lam, eta};
     sign_apply(&a, in, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* rational approximation, Eq. (12): Zolotarev's optimal P(x) ~ x^-1/2  */
+/* ------------------------------------------------------------------ */
+/* Complete elliptic integral K(m) of parameter m = k^2 (k the modulus), by the
+ * arithmetic-geometric mean: K = pi / (2 AGM(1, sqrt(1 - m))). */
+double or_ellipk(double m)
+{
+    double a = 1.0, b = sqrt(1.0 - m);
+    for (int i = 0; i < 60 && fabs(a - b) > 1e-16 * a; ++i) {
+        double an = 0.5 * (a + b);
+        b = sqrt(a * b);
+        a = an;
+    }
+    return M_PI / (2.0 * a);
+}
+
+/* Jacobi elliptic functions sn, cn, dn of argument u and parameter m, by the
+ * descending AGM (Abramowitz and Stegun 16.4.3): a_0 = 1, b_0 = sqrt(1-m),
+ * c_0 = sqrt(m); phi_N = 2^N a_N u; phi_{j-1} = (phi_j + asin(c_j sin(phi_j) / a_j)) / 2;
+ * sn = sin(phi_0), cn = cos(phi_0), dn = cn / cos(phi_1 - phi_0). */
+void or_jacobi(double u, double m, double *sn, double *cn, double *dn)
+{
+    double a[64], c[64];
+    a[0] = 1.0;
+    double b = sqrt(1.0 - m);
+    c[0] = sqrt(m);
+    int N = 0;
+    while (N < 62 && fabs(c[N]) > 1e-16) {
+        a[N + 1] = 0.5 * (a[N] + b);
+        c[N + 1] = 0.5 * (a[N] - b);
+        b = sqrt(a[N] * b);
+        ++N;
+    }
+    double phi = ldexp(1.0, N) * a[N] * u, phi1 = phi;
+    for (int j = N; j >= 1; --j) {
+        phi1 = phi;
+        phi = 0.5 * (phi + asin(c[j] * sin(phi) / a[j]));
+    }
+    *sn = sin(phi);
+    *cn = cos(phi);
+    *dn = N ? *cn / cos(phi1 - phi) : 1.0;
+}
+
+/* Zolotarev's optimal rational approximation of type (2n-1, 2n) to sign(q) on
+ * k <= |q| <= 1 (k = sqrt(eps)): sign(q) ~ D q prod_{j<n} (q^2 + a_{2j}) / prod_{i<=n} (q^2 + a_{2i-1}),
+ * a_l = eps sn^2(l K'/(2n); 1-eps) / cn^2(l K'/(2n); 1-eps), K' = K(1-eps).  As P(x) ~ x^-1/2
+ * on [eps, 1] (x = q^2) in partial fractions (the form of Eq. 12):
+ *   P(x) = sum_{i=1}^{n} b_i / (x + c_i),  c_i = a_{2i-1},
+ *   b_i = D prod_j (a_{2j} - c_i) / prod_{l != i} (c_l - c_i).
+ * D puts the error 1 - sqrt(x) P(x) in equioscillation: D = 2 / (max f + min f) for
+ * f(q) = q prod / prod on [k, 1], its extremes located on a grid and refined by golden
+ * section.  Returns delta = (max f - min f) / (max f + min f) (Eq. 4). */
+static double zolo_f(int n, const double *a, double q)
+{
+    double v = q;
+    for (int j = 1; j < n; ++j) v *= q * q + a[2 * j];
+    for (int i = 1; i <= n; ++i) v /= q * q + a[2 * i - 1];
+    return v;
+}
+
+static double golden_extreme(int n, const double *a, double lo, double hi, int maximise)
+{
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    double f1 = zolo_f(n, a, x1), f2 = zolo_f(n, a, x2);
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        if ((f1 > f2) == (maximise != 0)) {
+            hi = x2;
+            x2 = x1;
+            f2 = f1;
+            x1 = hi - g * (hi - lo);
+            f1 = zolo_f(n, a, x1);
+        } else {
+            lo = x1;
+            x1 = x2;
+            f1 = f2;
+            x2 = lo + g * (hi - lo);
+            f2 = zolo_f(n, a, x2);
+        }
+    }
+    return zolo_f(n, a, 0.5 * (lo + hi));
+}
+
+double or_zolotarev(double eps, int n, double *b, double *c)
+{
+    double *a = malloc(sizeof(double) * (2 * n + 1));
+    const double m = 1.0 - eps, Kp = or_ellipk(m);
+    for (int l = 1; l <= 2 * n - 1; ++l) {
+        double sn, cn, dn;
+        or_jacobi(l * Kp / (2.0 * n), m, &sn, &cn, &dn);
+        a[l] = eps * sn * sn / (cn * cn);
+    }
+    /* extremes of f on [k, 1]: the end points and the interior local extremes */
+    const double k = sqrt(eps);
+    const int G = 20000;
+    double fhi = fmax(zolo_f(n, a, k), zolo_f(n, a, 1.0)), flo = fmin(zolo_f(n, a, k), zolo_f(n, a, 1.0));
+    double qp = k, fp = zolo_f(n, a, k);
+    double qc = exp(log(k) * (1.0 - 1.0 / G)), fc = zolo_f(n, a, qc);
+    for (int i = 2; i <= G; ++i) {
+        double qn = exp(log(k) * (1.0 - (double)i / G)), fn = zolo_f(n, a, qn);
+        if (fc > fp && fc >= fn) fhi = fmax(fhi, golden_extreme(n, a, qp, qn, 1));
+        if (fc < fp && fc <= fn) flo = fmin(flo, golden_extreme(n, a, qp, qn, 0));
+        qp = qc;
+        fp = fc;
+        qc = qn;
+        fc = fn;
+    }
+    const double D = 2.0 / (fhi + flo);
+    for (int i = 1; i <= n; ++i) {
+        const double ci = a[2 * i - 1];
+        double v = D;
+        for (int j = 1; j < n; ++j) v *= a[2 * j] - ci;
+        for (int l = 1; l <= n; ++l)
+            if (l != i) v /= a[2 * l - 1] - ci;
+        c[i - 1] = ci;
+        b[i - 1] = v;
+    }
+    free(a);
+    return (fhi - flo) / (fhi + flo);
+}
+
+/* P(x) = sum_i b_i / (x + c_i) */
+double or_rational_eval(const double *b, const double *c, int n, double x)
+{
+    double v = 0;
+    for (int i = 0; i < n; ++i) v += b[i] / (x + c[i]);
+    return v;
+}
+
+/* pp = sum_i rb_i (Q^2 + rc_i)^-1 ph by one multi-shift CG (Eq. 12 and the
+ * multi-shifted CG of Sec. V): CG on the base system (Q^2 + c_0) x = ph, c_0 the smallest
+ * shift, the others (Q^2 + c_0 + s_i) x_i = ph with s_i = c_i - c_0 >= 0 from the same Krylov
+ * space (collinear residuals r_i = z_i r, the shifted-system recurrences of Jegerlehner 1996);
+ * each shift stops updating once |z_i| |r| <= rtol |ph|. */
+static void rational_apply(const sign_args *a, const cplx *ph, cplx *pp)
+{
+    long N = 12 * volume(a->d);
+    const int n = a->npoles;
+    int i0 = 0;
+    for (int i = 1; i < n; ++i)
+        if (a->rc[i] < a->rc[i0]) i0 = i;
+    const double c0 = a->rc[i0];
+    cplx *r = malloc(sizeof(cplx) * N), *p = malloc(sizeof(cplx) * N), *q = malloc(sizeof(cplx) * N);
+    cplx *tmp = malloc(sizeof(cplx) * N), *ps = malloc(sizeof(cplx) * N * n), *xs = calloc((size_t)N * n, sizeof(cplx));
+    double *z = malloc(sizeof(double) * n), *zo = malloc(sizeof(double) * n), *zn = malloc(sizeof(double) * n);
+    int *act = malloc(sizeof(int) * n);
+    memcpy(r, ph, sizeof(cplx) * N);
+    memcpy(p, ph, sizeof(cplx) * N);
+    for (int i = 0; i < n; ++i) {
+        memcpy(ps + (long)i * N, ph, sizeof(cplx) * N);
+        z[i] = zo[i] = 1.0;
+        act[i] = 1;
+    }
+    const double bn = sqrt(vnorm2(N, ph));
+    double rr = bn * bn, alpha_o = 1.0, beta_o = 0.0;
+    const double s2 = 1.0 / (a->lmax * a->lmax);
+    for (int it = 0; it < 100000 && bn > 0; ++it) {
+        int any = 0;
+        for (int i = 0; i < n; ++i) any |= act[i];
+        if (!any) break;
+        /* q = (Q^2 + c_0) p */
+        or_hw(a->d, a->bc, a->U, a->mw, p, tmp);
+        or_hw(a->d, a->bc, a->U, a->mw, tmp, q);
+        for (long k = 0; k < N; ++k) q[k] = s2 * q[k] + c0 * p[k];
+        const double alpha = rr / creal(vdot(N, p, q));
+        for (int i = 0; i < n; ++i) {
+            zn[i] = z[i];
+            if (!act[i]) continue;
+            const double si = a->rc[i] - c0;
+            zn[i] = z[i] * zo[i] * alpha_o / (alpha * beta_o * (zo[i] - z[i]) + zo[i] * alpha_o * (1.0 + si * alpha));
+            const double ai = alpha * zn[i] / z[i];
+            cplx *xi = xs + (long)i * N, *pi = ps + (long)i * N;
+            for (long k = 0; k < N; ++k) xi[k] += ai * pi[k];
+        }
+        for (long k = 0; k < N; ++k) r[k] -= alpha * q[k];
+        const double rn = vnorm2(N, r), beta = rn / rr;
+        for (int i = 0; i < n; ++i) {
+            if (act[i]) {
+                const double bi = beta * (zn[i] / z[i]) * (zn[i] / z[i]);
+                cplx *pi = ps + (long)i * N;
+                for (long k = 0; k < N; ++k) pi[k] = zn[i] * r[k] + bi * pi[k];
+                if (fabs(zn[i]) * sqrt(rn) <= a->rtol * bn) act[i] = 0;
+            }
+            if (zn[i] != z[i]) {
+                zo[i] = z[i];
+                z[i] = zn[i];
+            }
+        }
+        for (long k = 0; k < N; ++k) p[k] = r[k] + beta * p[k];
+        alpha_o = alpha;
+        beta_o = beta;
+        rr = rn;
+    }
+    memset(pp, 0, sizeof(cplx) * N);
+    for (int i = 0; i < n; ++i)
+        for (long k = 0; k < N; ++k) pp[k] += a->rb[i] * xs[(long)i * N + k];
+    free(r);
+    free(p);
+    free(q);
+    free(tmp);
+    free(ps);
+    free(xs);
+    free(z);
+    free(zo);
+    free(zn);
+    free(act);
+}
+
+/* out = sign(H_w(mw)) in with the rational P of Eq. (12) (partial fractions rb, rc) */
+void or_sign_rational(const int *d, const double *bc, const cplx *U, double mw, double lmax, int npoles,
+                      const double *rb, const double *rc, double rtol, int nev, const double *lam, const cplx *eta,
+                      const cplx *in, cplx *out)
+{
+    init_gamma();
+    sign_args a = {d, bc, U, mw, lmax, 0.0, 0, NULL, nev, lam, eta, npoles, rb, rc, rtol};
+    sign_apply(&a, in, out);
+}
+
+/* D(m) in with the rational sign (Eqs. 3, 8, 12) */
+void or_overlap_rational(const int *d, const double *bc, const cplx *U, double rho, double mass, double lmax,
+                         int npoles, const double *rb, const double *rc, double rtol, int nev, const double *lam,
+                         const cplx *eta, const cplx *in, cplx *out)
+{
+    init_gamma();
+    long V = volume(d), N = 12 * V;
+    sign_args a = {d, bc, U, -rho, lmax, 0.0, 0, NULL, nev, lam, eta, npoles, rb, rc, rtol};
+    cplx *s = malloc(sizeof(cplx) * N);
+    sign_apply(&a, in, s);
+    or_gamma5(V, s, s);
+    for (long i = 0; i < N; ++i) {
+        cplx Dpsi = in[i] + s[i];
+        out[i] = rho * Dpsi + mass * (in[i] - 0.5 * Dpsi);
+    }
+    free(s);
 }
 
 /* ------------------------------------------------------------------ */

@@ -54,6 +54,8 @@ _SIGS = {
     "ov_set_sign_poly": (_I, [_P, _D, _D, _I, _D]),
     "ov_get_sign_poly": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "ov_apply_overlap": (_I, [_P, _P, _P, _D, _I, _I, _P]),
+    "ov_set_sign_rational": (_I, [_P, _D, _D, _I, _D]),
+    "ov_get_sign_rational": (_I, [_P, ctypes.POINTER(_I), _P, _P, ctypes.POINTER(_D)]),
     "ov_apply_normal": (_I, [_P, _P, _P, _D, _I, _I, _I, _P]),
     "ov_deflate": (_I, [_P, _I, _I, _D, _P]),
     "ov_set_eigenpairs": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -249,6 +251,17 @@ class Context:
         self._check(self.lib.ov_get_sign_poly(self.h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(n),
                                               ctypes.byref(lm)))
         return {"rho": r.value, "eps": e.value, "degree": n.value, "lambda_max": lm.value}
+
+    def set_sign_rational(self, rho, eps, npoles, lambda_max=0.0):
+        self._check(self.lib.ov_set_sign_rational(self.h, float(rho), float(eps), int(npoles), float(lambda_max)))
+
+    def get_sign_rational(self):
+        n = _I()
+        d = _D()
+        self._check(self.lib.ov_get_sign_rational(self.h, ctypes.byref(n), None, None, ctypes.byref(d)))
+        b, c = np.empty(n.value), np.empty(n.value)
+        self._check(self.lib.ov_get_sign_rational(self.h, ctypes.byref(n), _ptr(b), _ptr(c), ctypes.byref(d)))
+        return b, c, d.value
 
     def apply_overlap(self, x, out, mass=0.0, prec="f64", stream=None):
         self._check(self.lib.ov_apply_overlap(self.h, _ptr(x), _ptr(out), float(mass), self._nrhs(x), _prec(prec),

@@ -338,19 +338,29 @@ static int overlap_core(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, do
         // for FP32 (bf16 rows plus their bf16 remainders) and 16-bit storage; FP64 and double-float stay on
         // the CUDA cores
         const bool tc_ok = c->proj_tc && E.nev <= 128 && R <= 16 && c->g.Vh % 8 == 0;
-        const bool tc_dots = tc_ok && (P == P_F16 || P == P_BF16 || dots16);
-        const bool tc_upd = tc_ok && (P == P_F16 || P == P_BF16 || P == P_F32);
-        if (tc_dots) {
-            OV_TRY(proj_dots_tc(c, 0, in, dcoef, st));
+        const bool tc = tc_ok && (P == P_F16 || P == P_BF16 || P == P_F32);
+        (void)dots16;
+        if (tc) {
+            // FP32 work fields (also those of the 16-bit operator): bf16 rows plus their remainders
+            OV_TRY(proj_dots_tc(c, 0, in, dcoef, st, P == P_F32 ? 2 : 1));
         } else {
             OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
             OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
         }
-        if (tc_upd)
+        if (tc)
             OV_TRY(proj_update_tc(c, 0, in, dcoef, E.d_sign, ph, w, st));
         else
             OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));
         src = ph;
+    }
+    if (c->sign_backend == 1) {
+        // Eq. 12: P(Q^2) psi_h = sum_i b_i (Q^2 + c_i)^-1 psi_h by multi-shift CG, then the same final launch
+        OV_TRY(ws_field(c, WS_RS, P, R, &B[0]));
+        OV_TRY(rational_solve(c, src, B[0], gprec, st));
+        const double kk = (rho - 0.5 * mass) / lam;
+        FieldDesc y[2] = {in, defl ? w : in};
+        double sy[2] = {rho + 0.5 * mass, rho - 0.5 * mass};
+        return dslash_apply(c, B[0], out, kk * aw, -0.5 * kk, 0, g5_out, defl ? 2 : 1, y, sy, st, gprec);
     }
     const double alpha = 4.0 / (lam * lam * (1.0 - eps));
     const double beta = -2.0 * (1.0 + eps) / (1.0 - eps);
@@ -464,7 +474,8 @@ template <typename F>
 static int with_graph(ov_ctx* c, int kind, const FieldDesc& in, const FieldDesc& out, double mass, int g5,
                       cudaStream_t st, F body)
 {
-    if (!c->use_graphs) return body(st);
+    // the rational sign is a host-driven iteration (convergence tests between launches): never captured
+    if (!c->use_graphs || c->sign_backend == 1) return body(st);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st != nullptr && (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone))
         return body(st);  // the caller is capturing: record the launches into its graph
@@ -663,6 +674,85 @@ static void set_inner_poly(ov_ctx* c)
     }
 }
 
+// ---- rational sign (Eq. 12): Zolotarev's optimal partial fractions of x^{-1/2} on [eps, 1] ----
+// K(m) and the Jacobi functions of parameter m by the arithmetic-geometric mean (Gauss; Abramowitz and
+// Stegun 17.6 and 16.4): the AGM sequence a_j, b_j, c_j = (a_{j-1} - b_{j-1})/2 from (1, sqrt(1-m), sqrt m),
+// K = pi / (2 a_N); am(u) from phi_N = 2^N a_N u by phi_{j-1} = (phi_j + asin(c_j sin phi_j / a_j)) / 2.
+static void agm_jacobi(double u, double m, double* sn, double* cn, double* K)
+{
+    std::vector<double> av{1.0}, cv{std::sqrt(m)};
+    double bb = std::sqrt(1.0 - m);
+    while (av.size() < 64 && std::fabs(cv.back()) > 1e-17) {
+        const double a0 = av.back();
+        av.push_back(0.5 * (a0 + bb));
+        cv.push_back(0.5 * (a0 - bb));
+        bb = std::sqrt(a0 * bb);
+    }
+    const int N = (int)av.size() - 1;
+    if (K) *K = M_PI / (2.0 * av[N]);
+    double phi = std::ldexp(av[N] * u, N);
+    for (int j = N; j >= 1; --j) phi = 0.5 * (phi + std::asin(cv[j] * std::sin(phi) / av[j]));
+    *sn = std::sin(phi);
+    *cn = std::cos(phi);
+}
+
+// sign(q) ~ D q prod_{j<n} (q^2 + z_j) / prod_{i<=n} (q^2 + p_i) on sqrt(eps) <= |q| <= 1 with
+// z_j = a_{2j}, p_i = a_{2i-1}, a_l = eps sn^2 / cn^2 (l K'/(2n) | 1 - eps), K' = K(1 - eps) (Zolotarev);
+// D makes the error equioscillate (2 / (max + min) of the unscaled function on [sqrt(eps), 1], its extremes
+// bracketed on a log grid and refined by golden section).  Output: P(x) = sum_i b_i / (x + c_i), delta.
+static double zolotarev_fractions(double eps, int n, std::vector<double>& b, std::vector<double>& cc)
+{
+    std::vector<double> a(2 * n + 1, 0.0);
+    double Kp = 0, sn = 0, cn = 0;
+    agm_jacobi(0.0, 1.0 - eps, &sn, &cn, &Kp);
+    for (int l = 1; l <= 2 * n - 1; ++l) {
+        agm_jacobi(l * Kp / (2.0 * n), 1.0 - eps, &sn, &cn, nullptr);
+        a[l] = eps * (sn * sn) / (cn * cn);
+    }
+    auto f = [&](double q) {
+        double v = q;
+        for (int j = 1; j < n; ++j) v *= q * q + a[2 * j];
+        for (int i = 1; i <= n; ++i) v /= q * q + a[2 * i - 1];
+        return v;
+    };
+    auto refine = [&](double lo, double hi, bool top) {
+        const double g = 0.6180339887498949;
+        for (int it = 0; it < 160; ++it) {
+            const double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+            if ((f(x1) > f(x2)) == top)
+                hi = x2;
+            else
+                lo = x1;
+        }
+        return f(0.5 * (lo + hi));
+    };
+    const double k = std::sqrt(eps);
+    double hi = std::max(f(k), f(1.0)), lo = std::min(f(k), f(1.0));
+    const int G = 12000;
+    std::vector<double> q(G + 1), v(G + 1);
+    for (int i = 0; i <= G; ++i) {
+        q[i] = k * std::pow(1.0 / k, (double)i / G);
+        v[i] = f(q[i]);
+    }
+    for (int i = 1; i < G; ++i) {
+        if (v[i] > v[i - 1] && v[i] >= v[i + 1]) hi = std::max(hi, refine(q[i - 1], q[i + 1], true));
+        if (v[i] < v[i - 1] && v[i] <= v[i + 1]) lo = std::min(lo, refine(q[i - 1], q[i + 1], false));
+    }
+    const double D = 2.0 / (hi + lo);
+    b.assign(n, 0.0);
+    cc.assign(n, 0.0);
+    for (int i = 1; i <= n; ++i) {
+        const double ci = a[2 * i - 1];
+        double w = D;
+        for (int j = 1; j < n; ++j) w *= a[2 * j] - ci;
+        for (int l = 1; l <= n; ++l)
+            if (l != i) w /= a[2 * l - 1] - ci;
+        cc[i - 1] = ci;
+        b[i - 1] = w;
+    }
+    return (hi - lo) / (hi + lo);
+}
+
 static int check_prec(ov_ctx* c, int prec)
 {
     if (prec < 0 || prec >= NPREC) return set_err(c, OV_EINVAL, "unknown precision %d", prec);
@@ -731,6 +821,7 @@ int ov_destroy(ov_ctx* c)
     if (c->partials) dev_free(c, c->partials, c->partials_bytes);
     if (c->tc_b) dev_free(c, c->tc_b, c->tc_b_bytes);
     if (c->tc_cb) dev_free(c, c->tc_cb, c->tc_cb_bytes);
+    if (c->rcoef) dev_free(c, c->rcoef, c->rcoef_bytes);
     if (c->tc_err) dev_free(c, c->tc_err, sizeof(int));
     for (int i = 0; i < 2; ++i)
         if (c->stage[i]) dev_free(c, c->stage[i], c->stage_bytes[i]);
@@ -849,6 +940,7 @@ int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambd
     c->rho = rho;
     c->eps = eps;
     c->degree = degree;
+    c->sign_backend = 0;
     cheb_coefficients(eps, degree, c->coef);
     set_inner_poly(c);
     if (lambda_max > 0) {
@@ -860,6 +952,41 @@ int ov_set_sign_poly(ov_ctx* c, double rho, double eps, int degree, double lambd
         c->lmax = 1.01 * l;
     }
     c->have_poly = true;
+    return OV_OK;
+}
+
+int ov_set_sign_rational(ov_ctx* c, double rho, double eps, int npoles, double lambda_max)
+{
+    if (!c) return OV_EINVAL;
+    if (!(eps > 0.0 && eps < 1.0)) return set_err(c, OV_EINVAL, "eps = %g outside (0, 1)", eps);
+    if (npoles < 1 || npoles > 64) return set_err(c, OV_EINVAL, "npoles = %d out of range 1..64", npoles);
+    if (!(rho > 0.0 && rho < 2.0)) return set_err(c, OV_EINVAL, "rho = %g outside (0, 2)", rho);
+    double l = lambda_max;
+    if (!(l > 0)) {
+        if (!c->have_gauge) return set_err(c, OV_ESTATE, "lambda_max estimate needs the gauge field");
+        OV_TRY(estimate_lambda_max(c, 50, &l, (cudaStream_t)0));
+        l *= 1.01;
+    }
+    graphs_clear(c);
+    c->rho = rho;
+    c->eps = eps;
+    c->lmax = l;
+    c->rdelta = zolotarev_fractions(eps, npoles, c->rb, c->rc);
+    c->sign_backend = 1;
+    c->have_poly = true;
+    return OV_OK;
+}
+
+int ov_get_sign_rational(const ov_ctx* c, int* npoles, double* b, double* cc, double* delta)
+{
+    if (!c || !npoles) return OV_EINVAL;
+    if (c->sign_backend != 1) return OV_ESTATE;
+    *npoles = (int)c->rb.size();
+    for (size_t i = 0; i < c->rb.size(); ++i) {
+        if (b) b[i] = c->rb[i];
+        if (cc) cc[i] = c->rc[i];
+    }
+    if (delta) *delta = c->rdelta;
     return OV_OK;
 }
 
@@ -1117,8 +1244,8 @@ int ov_project_lowmodes(ov_ctx* c, int which, const ov_field* psi, int engine, d
     const size_t ncoef = (size_t)E.nev * R;
     if (ncoef * 2 > (size_t)DSCAL_COEF) return set_err(c, OV_EINVAL, "nev * nrhs = %zu too large", ncoef);
     double2* dev = (double2*)c->dscal;
-    if (engine == 1) {
-        OV_TRY(proj_dots_tc(c, which, psi->d, dev, st));
+    if (engine == 1 || engine == 2) {
+        OV_TRY(proj_dots_tc(c, which, psi->d, dev, st, engine));
         OV_TRY(proj_tc_status(c, st));
     } else if (engine == 0) {
         FieldDesc eta;
@@ -1130,7 +1257,7 @@ int ov_project_lowmodes(ov_ctx* c, int which, const ov_field* psi, int engine, d
         OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, psi->d, (double2*)c->partials, nblk, st));
         OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dev, st));
     } else {
-        return set_err(c, OV_EINVAL, "engine = %d (0 CUDA cores, 1 tensor cores)", engine);
+        return set_err(c, OV_EINVAL, "engine = %d (0 CUDA cores, 1 or 2 tensor cores)", engine);
     }
     OV_CUDA(c, cudaMemcpyAsync(out, dev, ncoef * sizeof(double2), cudaMemcpyDefault, st));
     OV_CUDA(c, cudaStreamSynchronize(st));
@@ -1202,6 +1329,12 @@ int ov_set_option(ov_ctx* c, const char* name, double value)
         c->net_sym = value != 0;
     } else if (n == "chiral") {
         c->chiral = value != 0;
+    } else if (n == "rational_pass") {
+        if (value != 1 && value != 2) return set_err(c, OV_EINVAL, "rational_pass must be 1 or 2");
+        c->rational_pass = (int)value;
+    } else if (n == "rational_tol") {
+        if (!(value > 0 && value < 1)) return set_err(c, OV_EINVAL, "rational_tol must lie in (0, 1)");
+        c->rational_tol = value;
     } else if (n == "clenshaw_f32") {
         graphs_clear(c);
         c->clenshaw_f32 = value != 0;
@@ -1239,6 +1372,9 @@ int ov_get_option(const ov_ctx* c, const char* name, double* value)
     else if (n == "wait_polls") *value = (double)c->wait_polls;
     else if (n == "adaptive_delta") *value = c->adaptive_delta;
     else if (n == "clenshaw_f32") *value = c->clenshaw_f32;
+    else if (n == "rational_pass") *value = c->rational_pass;
+    else if (n == "rational_tol") *value = c->rational_tol;
+    else if (n == "rational_iterations") *value = (double)c->rational_iters;
     else if (n == "adaptive_degree") *value = c->degree_in;
     else return OV_EINVAL;
     return OV_OK;

@@ -34,7 +34,7 @@ constexpr int DSCAL_TMP = 64512;    // single-value scratch
 enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
-    WS_CG_BH, WS_CG_XH, WS_TC0, WS_TC1, WS_MX0, WS_MX1,
+    WS_CG_BH, WS_CG_XH, WS_TC0, WS_TC1, WS_MX0, WS_MX1, WS_RS, WS_RR, WS_RP, WS_RQ, WS_RT,
     WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
@@ -67,6 +67,13 @@ struct ov_ctx {
     double rho = 1.5, eps = 0.05, lmax = 0.0;
     int degree = 0;
     std::vector<double> coef;
+    // rational sign (Eq. 12): sign_backend 1 uses P(x) = sum_i rb_i / (x + rc_i) by multi-shift CG
+    int sign_backend = 0;
+    std::vector<double> rb, rc;
+    double rdelta = 0.0;
+    int rational_pass = 2;        // 1 single pass (2n shifted vectors), 2 double pass (scalars, then one sum)
+    double rational_tol = 1e-12;  // relative residual of every shifted solve
+    long long rational_iters = 0; // CG iterations of the last rational sign application (instrumentation)
     // adaptive-precision CG: the inner operator's polynomial (degree_in <= degree, delta <= adaptive_delta)
     double adaptive_delta = 0.0;
     int degree_in = 0;
@@ -118,6 +125,8 @@ struct ov_ctx {
     size_t tc_b_bytes = 0;
     void* tc_cb = nullptr;  // bf16 coefficient operand of the tensor-core V c update
     size_t tc_cb_bytes = 0;
+    void* rcoef = nullptr;  // device coefficient blocks of the rational sign's multi-shift CG
+    size_t rcoef_bytes = 0;
     int* tc_err = nullptr;
 
     std::string err;
@@ -176,6 +185,8 @@ int norm2(ov_ctx* c, const FieldDesc& x, double* dout, cudaStream_t st);
 int convert(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st);
 int copy_field(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, cudaStream_t st);
 
+// s = sum_i b_i (Q^2 + c_i)^-1 src, the rational P(Q^2) of Eq. 12 (solver.cu); gprec: link precision
+int rational_solve(ov_ctx* c, const FieldDesc& src, const FieldDesc& s, int gprec, cudaStream_t st);
 // solvers (solver.cu)
 int estimate_lambda_max(ov_ctx* c, int steps, double* lmax, cudaStream_t st);
 int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st);
@@ -190,7 +201,8 @@ void net_free(ov_ctx* c);
 // eigenpairs
 void eig_clear(ov_ctx* c, EigSet& E);
 // tensor-core projection (proj_tc.cu): c[i][r] = eta_i^dag psi_r, device double2 [nev][R]
-int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st);
+// nsplit 1: bf16 rows and bf16 psi; 2: plus the bf16 remainders of both (FP32-class coefficients)
+int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st, int nsplit = 1);
 int proj_tc_status(ov_ctx* c, cudaStream_t st);
 // out1 = psi - sum_i eta_i c_i, out2 = gamma5 sum_i s_i c_i eta_i on the tensor cores (FP32 / 16-bit fields)
 int proj_update_tc(ov_ctx* c, int which, const FieldDesc& psi, const double2* dcoef, const double* dsign,

@@ -66,7 +66,7 @@ extern "C" int ov_field_dot_noalloc(const ov_field* x, const ov_field* y, double
     }
     if (dev != c->device) return OV_EINVAL;  // fields live on another device
     const int nblk = reduce_blocks(c->g);
-    if ((long long)nblk * a.nrhs > kPartials || 2 * a.nrhs > 2 * kResult) return OV_EINVAL;
+    if ((long long)nblk * a.nrhs > kPartials || a.nrhs > kResult) return OV_EINVAL;
     double2* scratch = scratch_for_current_device(dev);
     if (!scratch) return OV_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;

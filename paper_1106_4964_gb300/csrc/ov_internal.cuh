@@ -330,6 +330,28 @@ __device__ __forceinline__ void load_spinor(const char* __restrict__ base, const
     }
 }
 
+// 16-bit storage: the 24 stored values without their site scale, which is returned
+template <int P>
+__device__ __forceinline__ float load_spinor_unscaled(const char* __restrict__ base, const float* __restrict__ nrm,
+                                                      int Vh, int s, float v[24])
+{
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 t = __ldg(b + (size_t)k * Vh + s);
+        const float2 a0 = Half<P>::to2(t.x), a1 = Half<P>::to2(t.y), a2 = Half<P>::to2(t.z), a3 = Half<P>::to2(t.w);
+        v[8 * k + 0] = a0.x;
+        v[8 * k + 1] = a0.y;
+        v[8 * k + 2] = a1.x;
+        v[8 * k + 3] = a1.y;
+        v[8 * k + 4] = a2.x;
+        v[8 * k + 5] = a2.y;
+        v[8 * k + 6] = a3.x;
+        v[8 * k + 7] = a3.y;
+    }
+    return __ldg(nrm + s);
+}
+
 template <int P, typename Real>
 __device__ __forceinline__ void store_spinor(char* __restrict__ base, float* __restrict__ nrm, int Vh, int s,
                                              const Real v[24])
@@ -419,17 +441,32 @@ __device__ __forceinline__ void load_link_rows(const char* __restrict__ base, in
 
 // row 2 = conj(row0 x row1)  (unitarity and det = 1)
 template <typename Real>
+__device__ __forceinline__ Real fma_any(Real a, Real b, Real c)
+{
+    if constexpr (std::is_same<Real, df64>::value)
+        return a * b + c;
+    else
+        return fma(a, b, c);
+}
+template <typename Real>
 __device__ __forceinline__ void link_row2(Real u[18])
 {
-    // (r0 x r1)_0 = r0_1 r1_2 - r0_2 r1_1, _1 = r0_2 r1_0 - r0_0 r1_2, _2 = r0_0 r1_1 - r0_1 r1_0
+    // (r0 x r1)_0 = r0_1 r1_2 - r0_2 r1_1, _1 = r0_2 r1_0 - r0_0 r1_2, _2 = r0_0 r1_1 - r0_1 r1_0; each real
+    // part one chain of a multiply and three fused multiply-adds
 #define OV_RE(i) u[2 * (i)]
 #define OV_IM(i) u[2 * (i) + 1]
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         int a = (j + 1) % 3, b = (j + 2) % 3;
         // r0_a r1_b - r0_b r1_a
-        Real re = OV_RE(a) * OV_RE(3 + b) - OV_IM(a) * OV_IM(3 + b) - (OV_RE(b) * OV_RE(3 + a) - OV_IM(b) * OV_IM(3 + a));
-        Real im = OV_RE(a) * OV_IM(3 + b) + OV_IM(a) * OV_RE(3 + b) - (OV_RE(b) * OV_IM(3 + a) + OV_IM(b) * OV_RE(3 + a));
+        Real re = OV_IM(b) * OV_IM(3 + a);
+        re = fma_any<Real>(-OV_RE(b), OV_RE(3 + a), re);
+        re = fma_any<Real>(-OV_IM(a), OV_IM(3 + b), re);
+        re = fma_any<Real>(OV_RE(a), OV_RE(3 + b), re);
+        Real im = -(OV_IM(b) * OV_RE(3 + a));
+        im = fma_any<Real>(-OV_RE(b), OV_IM(3 + a), im);
+        im = fma_any<Real>(OV_IM(a), OV_RE(3 + b), im);
+        im = fma_any<Real>(OV_RE(a), OV_IM(3 + b), im);
         u[12 + 2 * j] = re;
         u[12 + 2 * j + 1] = -im;
     }

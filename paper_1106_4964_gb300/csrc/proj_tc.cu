@@ -127,9 +127,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 }
 
 // partials[blockIdx.x][row][col] (FP32), row < 128, col < npad; K range split evenly over the grid
+// nsplit = 2: a second A operand (the bf16 remainder rows, tmAlo) accumulates into TMEM columns
+// [npad, 2 npad); partials then hold [128][2 npad] per CTA
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    proj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ktiles,
-                   int npad, int tmem_cols, float* __restrict__ partials, int* err)
+    proj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+                   const __grid_constant__ CUtensorMap tmB, int ktiles, int npad, int nsplit, int tmem_cols,
+                   float* __restrict__ partials, int* err)
 {
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
     const int a_bytes = TC_M * TC_BK * 2;
     const int b_bytes = npad * TC_BK * 2;
-    const int stage_bytes = a_bytes + b_bytes;
+    const int stage_bytes = nsplit * a_bytes + b_bytes;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (ktiles + gridDim.x - 1) / gridDim.x;
@@ -181,7 +184,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_expect_tx(&full_bar[s], stage_bytes);
             const int k = (t0 + t) * TC_BK;
             tma_load_2d(sa, &tmA, k, 0, &full_bar[s]);
-            tma_load_2d(sa + a_bytes, &tmB, k, 0, &full_bar[s]);
+            if (nsplit == 2) tma_load_2d(sa + a_bytes, &tmAlo, k, 0, &full_bar[s]);
+            tma_load_2d(sa + nsplit * a_bytes, &tmB, k, 0, &full_bar[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -196,10 +200,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint8_t* sa = base + s * stage_bytes;
-            uint8_t* sb = sa + a_bytes;
+            uint8_t* sb = sa + nsplit * a_bytes;
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 mma_bf16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                if (nsplit == 2)
+                    mma_bf16(tmem + (uint32_t)npad, smem_desc(sa + a_bytes + kk * 32), smem_desc(sb + kk * 32), idesc,
+                             (t > 0 || kk > 0) ? 1u : 0u);
+            }
             mma_commit(&empty_bar[s]);  // frees the stage when these MMAs have read it
             ++issued;
         }
@@ -210,13 +218,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = mbar_wait(&done_bar, 0);
     if (!ok && threadIdx.x == 0) atomicExch(err, 3);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float* out = partials + (size_t)blockIdx.x * TC_M * npad;
+    const int ncol = nsplit * npad;
+    float* out = partials + (size_t)blockIdx.x * TC_M * ncol;
     const int row = warp * 32 + lane;
-    for (int c0 = 0; c0 < npad; c0 += 16) {
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) out[(size_t)row * npad + c0 + j] = (ok && issued >= 0 && nt > 0) ? v[j] : 0.f;
+        for (int j = 0; j < 16; ++j) out[(size_t)row * ncol + c0 + j] = (ok && issued >= 0 && nt > 0) ? v[j] : 0.f;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -224,23 +233,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
-// c[i][r] = (sum_g P[g][i][2r], sum_g P[g][i][2r+1]) in FP64, fixed order
-__global__ void proj_tc_reduce(const float* partials, int ngrid, int npad, int nev, int nrhs, double2* c)
+// c[i][r] = (sum_g P[g][i][2r], sum_g P[g][i][2r+1]) in FP64, fixed order.  nsplit = 2: the columns
+// 2R + 2r, 2R + 2r + 1 hold the products with the bf16 remainder of psi, and the second accumulator
+// (columns npad + ...) the products of the remainder rows of eta; the three leading terms are added
+// (hi.hi + hi.lo + lo.hi; lo.lo is below the FP32 resolution)
+__global__ void proj_tc_reduce(const float* partials, int ngrid, int npad, int nsplit, int nev, int nrhs, double2* c)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nev * nrhs) return;
     const int i = k / nrhs, r = k % nrhs;
+    const int ncol = nsplit * npad;
     double re = 0, im = 0;
     for (int g = 0; g < ngrid; ++g) {
-        const float* p = partials + ((size_t)g * TC_M + i) * npad;
+        const float* p = partials + ((size_t)g * TC_M + i) * ncol;
         re += p[2 * r];
         im += p[2 * r + 1];
+        if (nsplit == 2) {
+            re += (double)p[2 * nrhs + 2 * r] + (double)p[npad + 2 * r];
+            im += (double)p[2 * nrhs + 2 * r + 1] + (double)p[npad + 2 * r + 1];
+        }
     }
     c[k] = make_double2(re, im);
 }
 
-// B operand: rows 2r = psi_r, 2r+1 = (im, -re) pairs, bf16, from an FP32 field
-__global__ void build_b_kernel(const float4* __restrict__ x, int n4, int nrhs, __nv_bfloat16* B, long long K)
+// B operand: rows 2r = psi_r, 2r+1 = (im, -re) pairs, bf16, from an FP32 field; nsplit = 2 adds rows
+// 2R + 2r, 2R + 2r + 1 with the bf16 remainders x - bf16(x) of the same values
+__device__ __forceinline__ float bf16_rem(float x) { return x - __bfloat162float(__float2bfloat16_rn(x)); }
+__global__ void build_b_kernel(const float4* __restrict__ x, int n4, int nrhs, int nsplit, __nv_bfloat16* B,
+                               long long K)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
@@ -252,6 +272,14 @@ __global__ void build_b_kernel(const float4* __restrict__ x, int n4, int nrhs, _
     b1[1] = __floats2bfloat162_rn(v.z, v.w);
     b2[0] = __floats2bfloat162_rn(v.y, -v.x);
     b2[1] = __floats2bfloat162_rn(v.w, -v.z);
+    if (nsplit == 2) {
+        __nv_bfloat162* l1 = reinterpret_cast<__nv_bfloat162*>(B + (size_t)(2 * nrhs + 2 * r) * K + 4 * q);
+        __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(B + (size_t)(2 * nrhs + 2 * r + 1) * K + 4 * q);
+        l1[0] = __floats2bfloat162_rn(bf16_rem(v.x), bf16_rem(v.y));
+        l1[1] = __floats2bfloat162_rn(bf16_rem(v.z), bf16_rem(v.w));
+        l2[0] = __floats2bfloat162_rn(bf16_rem(v.y), bf16_rem(-v.x));
+        l2[1] = __floats2bfloat162_rn(bf16_rem(v.w), bf16_rem(-v.z));
+    }
 }
 
 // the bf16 remainder x - bf16(x) of each FP32 value
@@ -645,7 +673,7 @@ int proj_update_tc(ov_ctx* c, int which, const FieldDesc& psi, const double2* dc
         return set_err(c, OV_ECUDA, "cuTensorMapEncodeTiled failed");
     const uint32_t stage_bytes = (uint32_t)nsplit * 2 * kpadA * 128;
     const uint32_t bbytes = (uint32_t)kchunksB * npad * 128;
-    constexpr int kSmemMax = 227 * 1024;
+    constexpr int kSmemMax = 224 * 1024;  // dynamic part; the barriers' static shared memory comes on top
     const int stages = std::min(4, (int)((kSmemMax - 1024 - (int)bbytes) / (int)stage_bytes));
     if (stages < 2) return set_err(c, OV_EINVAL, "tensor-core update: tiles do not fit in shared memory");
     const size_t smem = (size_t)stages * stage_bytes + bbytes + 1024;
@@ -701,24 +729,28 @@ int proj_update_tc(ov_ctx* c, int which, const FieldDesc& psi, const double2* dc
 }
 
 // c[i][r] = eta_i^dag psi_r (double2 [nev][R] device) on the tensor cores; psi any precision
-int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st)
+int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cudaStream_t st, int nsplit)
 {
     EigSet& E = c->eig[which];
     const int nev = E.nev, R = psi.nrhs;
     if (nev < 1 || nev > TC_M) return set_err(c, OV_EINVAL, "tensor-core projection: nev = %d outside 1..128", nev);
-    const int npad = ((2 * R + 15) / 16) * 16;
-    if (npad > 256) return set_err(c, OV_EINVAL, "tensor-core projection: too many right-hand sides");
+    if (nsplit != 1 && nsplit != 2) return set_err(c, OV_EINVAL, "tensor-core projection: nsplit %d", nsplit);
+    const int ncolB = 2 * nsplit * R;  // B rows: (psi, i psi) per rhs, and their bf16 remainders
+    const int npad = ((ncolB + 15) / 16) * 16;
+    if (npad * nsplit > 256) return set_err(c, OV_EINVAL, "tensor-core projection: too many right-hand sides");
     const long long K = 48LL * c->g.Vh;
     if (K % TC_BK) return set_err(c, OV_EINVAL, "tensor-core projection: 24V must be a multiple of 64");
     const void* A = nullptr;
+    const void* Alo = nullptr;
     OV_TRY(eig_bf16_rows(c, which, st, &A));
+    if (nsplit == 2) OV_TRY(eig_bf16_lo_rows(c, which, st, &Alo));
     // psi as FP32 (internal order), then the bf16 B rows
     FieldDesc p32 = psi;
     if (psi.prec != P_F32) {
         OV_TRY(ws_field(c, WS_AUX0, P_F32, R, &p32));
         OV_TRY(convert(c, psi, p32, st));
     }
-    const size_t bbytes = (size_t)2 * R * K * 2;
+    const size_t bbytes = (size_t)ncolB * K * 2;
     if (c->tc_b_bytes < bbytes) {
         if (c->tc_b) {
             cudaDeviceSynchronize();
@@ -731,30 +763,36 @@ int proj_dots_tc(ov_ctx* c, int which, const FieldDesc& psi, double2* cout, cuda
         c->tc_b_bytes = bbytes;
     }
     const long long n4 = K / 4;
-    build_b_kernel<<<dim3((unsigned)((n4 + 255) / 256), R), 256, 0, st>>>((const float4*)p32.data, (int)n4, R,
+    build_b_kernel<<<dim3((unsigned)((n4 + 255) / 256), R), 256, 0, st>>>((const float4*)p32.data, (int)n4, R, nsplit,
                                                                            (__nv_bfloat16*)c->tc_b, K);
     OV_CUDA(c, cudaGetLastError());
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, K, nev, TC_M) || !make_map(&mb, c->tc_b, K, 2 * R, npad))
+    CUtensorMap ma, malo, mb;
+    if (!make_map(&ma, A, K, nev, TC_M) || !make_map(&malo, nsplit == 2 ? Alo : A, K, nev, TC_M) ||
+        !make_map(&mb, c->tc_b, K, ncolB, npad))
         return set_err(c, OV_ECUDA, "cuTensorMapEncodeTiled failed");
     const int ktiles = (int)(K / TC_BK);
     const int grid = std::min(ktiles, 2 * 152);
-    const size_t smem = (size_t)TC_STAGES * (TC_M + npad) * TC_BK * 2 + 1024;
-    OV_TRY(ensure_partials(c, (size_t)grid * TC_M * npad * sizeof(float)));
+    const size_t smem = (size_t)TC_STAGES * (nsplit * TC_M + npad) * TC_BK * 2 + 1024;
+    OV_TRY(ensure_partials(c, (size_t)grid * TC_M * nsplit * npad * sizeof(float)));
     if (!c->tc_err) {
         void* p = nullptr;
         OV_TRY(dev_alloc(c, &p, sizeof(int)));
         c->tc_err = (int*)p;
         OV_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), st));
     }
-    // once per process, for the largest ring (npad = 256): no attribute call inside a graph capture
+    // once per process, for the largest ring: no attribute call inside a graph capture
     static const cudaError_t attr = cudaFuncSetAttribute(proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          TC_STAGES * (TC_M + 256) * TC_BK * 2 + 1024);
     OV_CUDA(c, attr);
-    const int tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : (npad <= 128 ? 128 : 256));
-    proj_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, mb, ktiles, npad, tmem_cols, (float*)c->partials, c->tc_err);
+    if (smem > (size_t)(TC_STAGES * (TC_M + 256) * TC_BK * 2 + 1024))
+        return set_err(c, OV_EINVAL, "tensor-core projection: tiles do not fit in shared memory");
+    const int ncol = nsplit * npad;
+    const int tmem_cols = ncol <= 32 ? 32 : (ncol <= 64 ? 64 : (ncol <= 128 ? 128 : 256));
+    proj_tc_kernel<<<grid, TC_THREADS, smem, st>>>(ma, malo, mb, ktiles, npad, nsplit, tmem_cols,
+                                                   (float*)c->partials, c->tc_err);
     OV_CUDA(c, cudaGetLastError());
-    proj_tc_reduce<<<(nev * R + 127) / 128, 128, 0, st>>>((const float*)c->partials, grid, npad, nev, R, cout);
+    proj_tc_reduce<<<(nev * R + 127) / 128, 128, 0, st>>>((const float*)c->partials, grid, npad, nsplit, nev, R,
+                                                          cout);
     OV_CUDA(c, cudaGetLastError());
     return OV_OK;
 }

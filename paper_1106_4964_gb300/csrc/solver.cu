@@ -1100,7 +1100,11 @@ int multimass_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc* xout, int 
         MM_TRY(block_sub(c, xi64, nd, bh, st));
     }
     // chiral mode: the inner operator A0 is the one-sign form on each source's sector
-    if (c->chiral) MM_TRY(chiral_setup(c, bh, q, 0.0, st));
+    if (c->chiral) {
+        FieldDesc tmp;
+        MM_TRY(ws_field(c, WS_CG_U, Ph, R, &tmp));  // a field of bh's precision for the chirality test
+        MM_TRY(chiral_setup(c, bh, tmp, 0.0, st));
+    }
     const double2* dch = (const double2*)(c->dscal + DSCAL_CHCO);
     const int ipoly = c->adaptive_delta > 0 ? 1 : 0;
     auto A0 = [&](const FieldDesc& in, const FieldDesc& out) -> int {
@@ -1303,6 +1307,316 @@ int multimass_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc* xout, int 
         for (int k = 0; k < M; ++k) info[k].seconds = sec;
     }
     return worst == OV_OK ? OV_OK : set_err(c, worst, "multimass: a mass did not converge");
+}
+
+// ---------------------------------------------------------------------------
+// rational sign (Eq. 12): s = sum_i b_i (Q^2 + c_i)^-1 src by multi-shift CG
+// ---------------------------------------------------------------------------
+// One CG on the base system (Q^2 + c_0) x = src, c_0 the smallest pole; the others are shifted systems
+// (Q^2 + c_0 + sigma_i) x_i = src, sigma_i = c_i - c_0 >= 0, whose residuals stay collinear with the base
+// residual, r_i = z_i r (Jegerlehner 1996; the same recurrences as the multi-mass solve).  Single pass
+// (the paper's "single pass"): the 2n shifted vectors p_i, x_i are updated every iteration and summed at
+// the end.  Double pass (Neuberger): the first pass runs the base CG alone and records its scalars; the
+// shifted scalars follow on the host, and with them the coefficient g_j of every base residual r_j in
+// s = sum_i b_i x_i (x_i = sum_k a_i^k p_i^k, p_i^k = zeta_i^k r_k + beta_i^(k-1) p_i^(k-1), so the
+// coefficient of r_j in x_i is zeta_i^j G_i^j with G_i^j = a_i^j + beta_i^j G_i^(j+1)); the second pass
+// repeats the base recursion with the recorded scalars (bit for bit the same r_j) and accumulates
+// s = sum_j g_j r_j: twice the dslash applications, three vector updates per iteration instead of 2n + 2.
+// Q^2 = H_w^2 / lambda_max^2; each application is two dslash launches, the shift fused into the second.
+int rational_solve(ov_ctx* c, const FieldDesc& src, const FieldDesc& s, int gprec, cudaStream_t st)
+{
+    const int R = src.nrhs, P = src.prec, n = (int)c->rb.size();
+    const double lam2 = c->lmax * c->lmax, aw = 4.0 - c->rho;
+    int i0 = 0;
+    for (int i = 1; i < n; ++i)
+        if (c->rc[i] < c->rc[i0]) i0 = i;
+    const double c0 = c->rc[i0];
+    std::vector<double> sg(n);
+    for (int i = 0; i < n; ++i) sg[i] = c->rc[i] - c0;
+    const double tol = P == P_F64 || P == P_DF64 ? c->rational_tol : std::max(c->rational_tol, 1e-6);
+    FieldDesc r, p, q, t;
+    OV_TRY(ws_field(c, WS_RR, P, R, &r));
+    OV_TRY(ws_field(c, WS_RP, P, R, &p));
+    OV_TRY(ws_field(c, WS_RQ, P, R, &q));
+    OV_TRY(ws_field(c, WS_RT, P, R, &t));
+    auto Aop = [&](const FieldDesc& in, const FieldDesc& out) -> int {  // (Q^2 + c_0) in
+        OV_TRY(dslash_apply(c, in, t, aw, -0.5, 1, 0, 0, nullptr, nullptr, st, gprec));
+        FieldDesc y[1] = {in};
+        double sy[1] = {c0};
+        return dslash_apply(c, t, out, aw / lam2, -0.5 / lam2, 1, 0, 1, y, sy, st, gprec);
+    };
+    const bool single = c->rational_pass == 1;
+    std::vector<FieldDesc> xs, ps;
+    int status = OV_OK;
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (auto& f : xs) field_free(c, &f);
+        for (auto& f : ps) field_free(c, &f);
+    };
+#define RS_TRY(x)             \
+    do {                      \
+        int s__ = (x);        \
+        if (s__ != OV_OK) {   \
+            release();        \
+            return s__;       \
+        }                     \
+    } while (0)
+    if (single) {
+        xs.resize(n);
+        ps.resize(n);
+        for (int i = 0; i < n; ++i) {
+            RS_TRY(field_alloc(c, P, R, &xs[i]));
+            RS_TRY(field_alloc(c, P, R, &ps[i]));
+            RS_TRY(copy_field(c, src, ps[i], st));
+            RS_TRY(cudaMemsetAsync(xs[i].data, 0, xs[i].rhs_bytes() * R, st) == cudaSuccess ? OV_OK : OV_ECUDA);
+            if (xs[i].norm)
+                RS_TRY(cudaMemsetAsync(xs[i].norm, 0, (size_t)2 * xs[i].Vh * 4 * R, st) == cudaSuccess ? OV_OK
+                                                                                                       : OV_ECUDA);
+        }
+    }
+    // device coefficient blocks ([K][R] double2 per lincomb), grown as needed
+    auto coef_buf = [&](size_t n2) -> double2* {
+        const size_t bytes = n2 * sizeof(double2);
+        if (bytes > c->rcoef_bytes) {
+            cudaStreamSynchronize(st);
+            if (c->rcoef) dev_free(c, c->rcoef, c->rcoef_bytes);
+            c->rcoef = nullptr;
+            c->rcoef_bytes = 0;
+            void* pp = nullptr;
+            if (dev_alloc(c, &pp, bytes) != OV_OK) return nullptr;
+            c->rcoef = pp;
+            c->rcoef_bytes = bytes;
+        }
+        return (double2*)c->rcoef;
+    };
+    double2* ddt = (double2*)(c->dscal + DSCAL_DOT);
+    double* dnr = c->dscal + DSCAL_NORM;
+    RS_TRY(copy_field(c, src, r, st));
+    RS_TRY(copy_field(c, src, p, st));
+    std::vector<double> rr(R), bn(R);
+    {
+        std::vector<double2> h(R);
+        RS_TRY(norm2(c, r, (double*)ddt, st));
+        RS_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+        for (int j = 0; j < R; ++j) {
+            rr[j] = h[j].x;
+            bn[j] = std::sqrt(h[j].x);
+        }
+    }
+    // per (shift, rhs) scalars; the recorded base scalars and shifted coefficients for the second pass
+    std::vector<double> z((size_t)n * R, 1.0), zo((size_t)n * R, 1.0), zn((size_t)n * R, 1.0);
+    std::vector<double> aold(R, 1.0), bold(R, 0.0);
+    std::vector<char> act((size_t)n * R, 1), live(R, 1);
+    for (int j = 0; j < R; ++j)
+        if (!(bn[j] > 0)) live[j] = 0;
+    std::vector<std::vector<double>> A_k, B_k;                     // base alpha, beta per iteration [R]
+    std::vector<std::vector<double>> ZE, AI, BI;                    // zeta_i^k, a_i^k, beta_i^k [n*R]
+    ZE.push_back(std::vector<double>((size_t)n * R, 1.0));          // zeta^0 = 1
+    int it = 0;
+    const int itmax = 20000;
+    for (; it < itmax; ++it) {
+        bool any = false;
+        for (int j = 0; j < R; ++j) any = any || live[j];
+        if (!any) break;
+        RS_TRY(Aop(p, q));
+        std::vector<double2> h(R);
+        RS_TRY(dot(c, p, q, ddt, st));
+        RS_TRY(to_host(c, ddt, h.data(), R * sizeof(double2), st));
+        std::vector<double> alpha(R, 0.0);
+        for (int j = 0; j < R; ++j) {
+            alpha[j] = (live[j] && h[j].x > 0) ? rr[j] / h[j].x : 0.0;
+            if (!std::isfinite(alpha[j])) {
+                release();
+                return set_err(c, OV_ENAN, "rational sign: NaN/Inf in the recursion");
+            }
+        }
+        std::vector<double> ai((size_t)n * R, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < R; ++j) {
+                const size_t ij = (size_t)i * R + j;
+                zn[ij] = z[ij];
+                if (act[ij] && alpha[j] != 0.0) {
+                    zn[ij] = z[ij] * zo[ij] * aold[j] /
+                             (alpha[j] * bold[j] * (zo[ij] - z[ij]) + zo[ij] * aold[j] * (1.0 + sg[i] * alpha[j]));
+                    ai[ij] = alpha[j] * zn[ij] / z[ij];
+                }
+            }
+        if (single) {  // x_i += a_i p_i
+            double2* dc = coef_buf((size_t)2 * n * R);
+            if (!dc) {
+                release();
+                return OV_ENOMEM;
+            }
+            std::vector<double2> hc((size_t)2 * n * R);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < R; ++j) {
+                    hc[(size_t)(2 * i) * R + j] = make_double2(1, 0);
+                    hc[(size_t)(2 * i + 1) * R + j] = make_double2(ai[(size_t)i * R + j], 0);
+                }
+            RS_TRY(to_dev(c, hc.data(), dc, hc.size() * sizeof(double2), st));
+            for (int i = 0; i < n; ++i) {
+                FieldDesc v[2] = {xs[i], ps[i]};
+                RS_TRY(lincomb(c, xs[i], 2, v, nullptr, dc + (size_t)(2 * i) * R, 0, nullptr, st));
+            }
+        }
+        // r -= alpha q, with |r|^2
+        std::vector<double2> hb(2 * R);
+        for (int j = 0; j < R; ++j) {
+            hb[j] = make_double2(1, 0);
+            hb[R + j] = make_double2(-alpha[j], 0);
+        }
+        double2* dco = (double2*)(c->dscal + DSCAL_CGCO);
+        RS_TRY(to_dev(c, hb.data(), dco, hb.size() * sizeof(double2), st));
+        {
+            FieldDesc v[2] = {r, q};
+            RS_TRY(lincomb(c, r, 2, v, nullptr, dco, 0, dnr, st));
+        }
+        std::vector<double> rn(R);
+        RS_TRY(to_host(c, dnr, rn.data(), R * sizeof(double), st));
+        std::vector<double> beta(R, 1.0), bi((size_t)n * R, 1.0);
+        for (int j = 0; j < R; ++j) {
+            if (!std::isfinite(rn[j])) {
+                release();
+                return set_err(c, OV_ENAN, "rational sign: NaN/Inf in the residual");
+            }
+            if (alpha[j] != 0.0) beta[j] = rr[j] > 0 ? rn[j] / rr[j] : 0.0;
+        }
+        std::vector<double> zeta_next((size_t)n * R, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < R; ++j) {
+                const size_t ij = (size_t)i * R + j;
+                if (act[ij] && alpha[j] != 0.0) {
+                    bi[ij] = beta[j] * (zn[ij] / z[ij]) * (zn[ij] / z[ij]);
+                    zeta_next[ij] = zn[ij];
+                    if (std::fabs(zn[ij]) * std::sqrt(rn[j]) <= tol * bn[j]) act[ij] = 0;
+                } else {
+                    bi[ij] = 1.0;  // p_i is frozen (its x_i no longer moves)
+                }
+                if (zn[ij] != z[ij]) {
+                    zo[ij] = z[ij];
+                    z[ij] = zn[ij];
+                }
+            }
+        if (single) {  // p_i = zn r + beta_i p_i
+            double2* dc = coef_buf((size_t)2 * n * R);
+            std::vector<double2> hc((size_t)2 * n * R);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < R; ++j) {
+                    const size_t ij = (size_t)i * R + j;
+                    const bool mv = bi[ij] != 1.0 || zeta_next[ij] != 0.0;
+                    hc[(size_t)(2 * i) * R + j] = make_double2(mv ? zeta_next[ij] : 0.0, 0);
+                    hc[(size_t)(2 * i + 1) * R + j] = make_double2(bi[ij], 0);
+                }
+            RS_TRY(to_dev(c, hc.data(), dc, hc.size() * sizeof(double2), st));
+            for (int i = 0; i < n; ++i) {
+                FieldDesc v[2] = {r, ps[i]};
+                RS_TRY(lincomb(c, ps[i], 2, v, nullptr, dc + (size_t)(2 * i) * R, 0, nullptr, st));
+            }
+        }
+        // p = r + beta p
+        for (int j = 0; j < R; ++j) {
+            hb[j] = make_double2(1, 0);
+            hb[R + j] = make_double2(alpha[j] != 0.0 ? beta[j] : 1.0, 0);
+            if (alpha[j] != 0.0) {
+                aold[j] = alpha[j];
+                bold[j] = beta[j];
+                rr[j] = rn[j];
+            }
+            bool done = true;
+            for (int i = 0; i < n; ++i) done = done && !act[(size_t)i * R + j];
+            if (done) live[j] = 0;
+        }
+        RS_TRY(to_dev(c, hb.data(), dco, hb.size() * sizeof(double2), st));
+        {
+            FieldDesc v[2] = {r, p};
+            RS_TRY(lincomb(c, p, 2, v, nullptr, dco, 0, nullptr, st));
+        }
+        A_k.push_back(alpha);
+        B_k.push_back(beta);
+        AI.push_back(ai);
+        BI.push_back(bi);
+        ZE.push_back(zeta_next);
+    }
+    c->rational_iters = it;
+    if (it >= itmax) {
+        release();
+        return set_err(c, OV_ENOTCONV, "rational sign: multi-shift CG not converged in %d iterations", itmax);
+    }
+    if (single) {  // s = sum_i b_i x_i, four fields per launch (s itself after the first)
+        int i = 0;
+        bool first = true;
+        while (i < n) {
+            FieldDesc v[4];
+            double2 hc[4];
+            int K = 0;
+            if (!first) {
+                v[K] = s;
+                hc[K++] = make_double2(1, 0);
+            }
+            while (K < 4 && i < n) {
+                v[K] = xs[i];
+                hc[K++] = make_double2(c->rb[i], 0);
+                ++i;
+            }
+            RS_TRY(lincomb(c, s, K, v, hc, nullptr, 0, nullptr, st));
+            first = false;
+        }
+        release();
+        return OV_OK;
+    }
+    // double pass: g_j per rhs from the recorded scalars, then the repeated base recursion
+    const int Kit = it;
+    std::vector<double> g((size_t)(Kit + 1) * R, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < R; ++j) {
+            double G = 0.0;  // G_i^(K) = 0
+            for (int k = Kit - 1; k >= 0; --k) {
+                const size_t ij = (size_t)i * R + j;
+                G = AI[k][ij] + BI[k][ij] * G;
+                g[(size_t)k * R + j] += c->rb[i] * ZE[k][ij] * G;
+            }
+        }
+    double2* dc = coef_buf((size_t)6 * R * (Kit + 1));
+    if (!dc) {
+        release();
+        return OV_ENOMEM;
+    }
+    std::vector<double2> hc((size_t)6 * R * (Kit + 1));
+    for (int k = 0; k <= Kit; ++k)
+        for (int j = 0; j < R; ++j) {
+            const double al = k < Kit ? A_k[k][j] : 0.0, be = k < Kit ? B_k[k][j] : 1.0;
+            double2* blk = hc.data() + (size_t)6 * R * k;
+            blk[j] = make_double2(1, 0);                  // r_{k+1} = r_k - alpha_k q
+            blk[R + j] = make_double2(-al, 0);
+            blk[2 * R + j] = make_double2(1, 0);          // p_{k+1} = r_{k+1} + beta_k p_k
+            blk[3 * R + j] = make_double2(be, 0);
+            blk[4 * R + j] = make_double2(1, 0);          // s += g_{k+1} r_{k+1}
+            blk[5 * R + j] = make_double2(k + 1 <= Kit ? g[(size_t)std::min(k + 1, Kit) * R + j] : 0.0, 0);
+        }
+    RS_TRY(to_dev(c, hc.data(), dc, hc.size() * sizeof(double2), st));
+    RS_TRY(copy_field(c, src, r, st));
+    RS_TRY(copy_field(c, src, p, st));
+    {
+        std::vector<double2> g0(R);
+        for (int j = 0; j < R; ++j) g0[j] = make_double2(g[j], 0);
+        double2* dco = (double2*)(c->dscal + DSCAL_CGCO);
+        RS_TRY(to_dev(c, g0.data(), dco, R * sizeof(double2), st));
+        FieldDesc v[1] = {src};
+        RS_TRY(lincomb(c, s, 1, v, nullptr, dco, 0, nullptr, st));  // s = g_0 r_0
+    }
+    for (int k = 0; k < Kit; ++k) {
+        const double2* blk = dc + (size_t)6 * R * k;
+        RS_TRY(Aop(p, q));
+        FieldDesc v1[2] = {r, q};
+        RS_TRY(lincomb(c, r, 2, v1, nullptr, blk, 0, nullptr, st));
+        FieldDesc v2[2] = {r, p};
+        RS_TRY(lincomb(c, p, 2, v2, nullptr, blk + 2 * R, 0, nullptr, st));
+        FieldDesc v3[2] = {s, r};
+        RS_TRY(lincomb(c, s, 2, v3, nullptr, blk + 4 * R, 0, nullptr, st));
+    }
+    release();
+#undef RS_TRY
+    return OV_OK;
 }
 
 }  // namespace ov

@@ -51,6 +51,15 @@ def test_tensor_core_projection(dims, nev, nrhs):
             assert rel(c1[:, r], exact[:, r]) < TC_TOL, (prec, r, rel(c1[:, r], exact[:, r]))
         # repeated calls give identical results (fixed-order FP64 reduction of the partials)
         assert np.array_equal(c1, ctx.project_lowmodes(1, f, engine=1))
+    # engine 2: bf16 rows and bf16 psi plus their remainders, FP32-class against the exact FP64 values of
+    # the FP32 field (the FP32 rounding of psi and of the rows stays: 1e-6 per coefficient vector)
+    f = ctx.field(nrhs, "f32")
+    f.load(dev(psi))
+    c2 = ctx.project_lowmodes(1, f, engine=2)
+    c0f = ctx.project_lowmodes(1, f, engine=0)
+    for r in range(nrhs):
+        assert rel(c2[:, r], exact[:, r]) < 2e-5, (r, rel(c2[:, r], exact[:, r]))
+        assert rel(c2[:, r], c0f[:, r]) < 2e-5
 
 
 def test_overlap_16bit_with_tensor_core_projection():
