@@ -68,7 +68,9 @@ typedef enum { OV_F64 = 0, OV_F32 = 1, OV_F16S = 2, OV_BF16S = 3, OV_DF64 = 4 } 
 typedef struct {
     int iterations;          /* CG iterations (max over right-hand sides) */
     int reliable_updates;    /* FP64 true-residual recomputations */
-    int fallback;            /* 1 if the learned preconditioner was switched off */
+    int fallback;            /* bit 1: the learned preconditioner was switched off; bit 2: the
+                                one-sign chiral form was (two reliable updates in a row that did not
+                                halve the true residual), the solve continued with the two-sign operator */
     int nrhs;
     double true_residual[64]; /* ||b - A x|| / ||b|| by the FP64 operator, per rhs */
     double seconds;          /* wall time of the solve */

@@ -786,8 +786,13 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // adaptive precision (Sec. V: adaptive CG): the inner operator may use a lower-degree polynomial; the
     // reliable updates recompute the true residual with the accurate one
     const int ipoly = c->adaptive_delta > 0 ? 1 : 0;
+    // the one-sign form rests on sign^2 = 1; where the inner precision's rounding of a high-degree
+    // polynomial breaks that by more than the smallest eigenvalue tolerates, the true residual stops
+    // falling: then the solve continues with the two-sign operator (fallback bit 2)
+    bool use_chiral = c->chiral != 0;
+    int chiral_stalls = 0;
     auto inner_apply = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-        return c->chiral ? chiral_apply(c, in, out, mass, dch, st, ipoly) : normal_apply(c, in, out, mass, st, ipoly);
+        return use_chiral ? chiral_apply(c, in, out, mass, dch, st, ipoly) : normal_apply(c, in, out, mass, st, ipoly);
     };
     // In chiral mode every vector of the inner recursion must stay in its right-hand side's sector:
     // the one-sign operator acts on the other sector as m^2 (plus a coupling back), so rounding-level
@@ -944,8 +949,19 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
                 // learned-preconditioner stall rule: the true residual must drop by x0.9 per check
                 if (use_prec && since >= 10 && worst > 0.9 * prev_worst) {
                     use_prec = false;
-                    fallback = 1;
+                    fallback |= 1;
                     restart = true;
+                }
+                // chiral-form stall rule: two reliable updates in a row that do not halve the true residual
+                // (updates come when the inner residual has dropped by reliable_delta; with the learned
+                // preconditioner they come every 10 iterations, and its own rule applies)
+                if (use_chiral && !use_prec) {
+                    chiral_stalls = worst > 0.5 * prev_worst ? chiral_stalls + 1 : 0;
+                    if (chiral_stalls >= 2) {
+                        use_chiral = false;
+                        fallback |= 2;
+                        restart = true;
+                    }
                 }
                 prev_worst = worst;
                 since = 0;

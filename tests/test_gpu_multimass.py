@@ -93,7 +93,7 @@ def test_multimass_twelve_sources_8c4():
 
     dims = (8, 8, 8, 8)
     U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
-    eps, n, lmax = 0.0005, 400, 6.6  # [eps, 1] covers this field's H_w spectrum (no H_w deflation)
+    eps, n, lmax = 0.005, 150, 6.6  # [eps, 1] covers this field's H_w spectrum (no H_w deflation)
     c = oracle.cheb_coeffs(eps, n)
     ctx = Context(dims, ABC)
     ctx.set_gauge(dev(U))
