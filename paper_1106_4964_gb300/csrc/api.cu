@@ -1396,6 +1396,7 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
         ((variant == 3 || variant == 4 || variant == 5) && by != 1))
         return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
     const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 || variant >= 6 ? 128 : 256);
+    if (variant >= 8 && by != 1) return set_err(c, OV_EINVAL, "variants 8, 9: by must be 1");
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
     c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
@@ -1419,6 +1420,10 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
         if (v >= 3 && wide(prec)) continue;  // staged variants: FP32 arithmetic only
         if (v == 4 || v == 5) {              // bulk-copy staging: fixed 128-site blocks
             cand.push_back(std::make_tuple(128, 1, v));
+            continue;
+        }
+        if (v == 8 || v == 9) {              // batched hop loads: 128-thread blocks, one rhs per block row
+            for (int x : {64, 128}) cand.push_back(std::make_tuple(x, 1, v));
             continue;
         }
         if (v >= 6) {                        // 2 or 4 right-hand sides per thread

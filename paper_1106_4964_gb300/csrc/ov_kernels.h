@@ -30,9 +30,10 @@ constexpr long long DSLASH_WAIT_POLLS = 1ll << 22;  // default first-wait limit 
 // var: 0 unbounded registers, 1 and 2 capped for occupancy, 3 per-thread cp.async staging
 // (FP32 math, by = 1), 4 block-wide bulk-copy (TMA) staging of the neighbour ranges (FP32 math;
 // fixed 128-site blocks, bx and by ignored), 5 the same with the eight links loaded before the wait,
-// 6 and 7: 2 and 4 right-hand sides per thread sharing each link (FP32 math; by counts rhs groups)
+// 6 and 7: 2 and 4 right-hand sides per thread sharing each link (FP32 math; by counts rhs groups),
+// 8 and 9: the loads of 4 or 8 hops issued together before their arithmetic (FP32 math)
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st);
-constexpr int DSLASH_VARIANTS = 8;
+constexpr int DSLASH_VARIANTS = 10;
 
 // ---------------------------------------------------------------- layout conversion
 // canonical complex128 [nrhs][V][12] (device) <-> internal field

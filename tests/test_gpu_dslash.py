@@ -167,7 +167,7 @@ def test_field_dot(prec, tol):
 
 # every launch variant the autotuner may pick: (bx, by, variant)
 VARIANTS = [(128, 1, 0), (64, 2, 0), (64, 1, 1), (32, 2, 2), (64, 1, 3), (128, 1, 4), (128, 1, 5), (64, 1, 6),
-            (32, 2, 6), (64, 1, 7)]
+            (32, 2, 6), (64, 1, 7), (64, 1, 8), (128, 1, 9)]
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6), (2, 6, 4, 10), (16, 16, 16, 32)])
