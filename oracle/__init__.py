@@ -22,6 +22,11 @@ Functions and what pins each one (tests/test_oracle_*.py):
                               |d - rho| = rho, D^dag D = rho (D + D^dag).
 ``overlap_normal`` / ``cg``   Eq. (9).  Dense linear solve on 2^4; true residual.
 ``multimass_cg``              Sec. II.  Dense solves of every mass; single-mass CG.
+``lambda_max``                Eq. (5).  Dense eigendecomposition: a lower bound of
+                              max |lambda| that reaches it when the Krylov space
+                              is the whole space.
+``lanczos_lowmodes``          Sec. V, Eq. (7).  Dense eigendecomposition on 2^4
+                              (whole space) and 4^4; eigen-residuals.
 ``ellipk`` / ``jacobi``       scipy.special's independent K(m) and ellipj.
 ``zolotarev``                 Eq. (12).  Closed form at n = 1; equioscillation of
                               the error with 2n + 1 extremes of equal size.
@@ -175,6 +180,33 @@ def _defl(evals, evecs, V):
     evecs = np.ascontiguousarray(evecs, dtype=np.complex128)
     assert evecs.size == len(evals) * 12 * V
     return len(evals), evals, evecs
+
+
+def lambda_max(dims, bc, U, mw, steps=50, v0=None):
+    """sqrt of the largest Ritz value of H_w^2 after `steps` Lanczos steps from v0 (Eq. 5 rescale)."""
+    V = volume(dims)
+    if v0 is None:
+        v0 = np.ones(12 * V, dtype=np.complex128)
+    v0 = _field(v0, V)
+    f = lib().or_lambda_max
+    f.restype = ctypes.c_double
+    return f(_dims(dims), _bc(bc), _ptr(_gauge(U, V)), ctypes.c_double(mw), ctypes.c_int(steps), _ptr(v0))
+
+
+def lanczos_lowmodes(dims, bc, U, mw, m, nev, v0=None):
+    """The nev smallest-|lambda| eigenpairs of H_w from m Lanczos steps on H_w^2 and Rayleigh-Ritz with
+    H_w (Eq. 7 needs the signs).  Returns (vals [nev], vecs [nev, 12V], max eigen-residual)."""
+    V = volume(dims)
+    if v0 is None:
+        v0 = np.ones(12 * V, dtype=np.complex128)
+    v0 = _field(v0, V)
+    vals = np.empty(nev)
+    vecs = np.empty((nev, 12 * V), dtype=np.complex128)
+    f = lib().or_lanczos_lowmodes
+    f.restype = ctypes.c_double
+    r = f(_dims(dims), _bc(bc), _ptr(_gauge(U, V)), ctypes.c_double(mw), ctypes.c_int(m), ctypes.c_int(nev), _ptr(v0),
+          _ptr(vals), _ptr(vecs))
+    return vals, vecs, r
 
 
 def ellipk(m: float) -> float:

@@ -396,6 +396,226 @@ void or_sign(const int *d, const double *bc, const cplx *U, double mw, double lm
 }
 
 /* ------------------------------------------------------------------ */
+/* Lanczos on H_w^2: the rescale lambda_max (Eq. 5) and the low modes   */
+/* (Eq. 7), Sec. V's eigensolver of H_w in its plainest form           */
+/* ------------------------------------------------------------------ */
+/* Eigen-decomposition of an n x n Hermitian matrix A (row major, destroyed) by
+ * cyclic Jacobi rotations: ev ascending, Z[k*n + i] = component k of eigenvector i. */
+static void herm_jacobi(int n, cplx *A, double *ev, cplx *Z)
+{
+    for (int i = 0; i < n * n; ++i) Z[i] = 0;
+    for (int i = 0; i < n; ++i) Z[i * n + i] = 1;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double a = creal(A[i * n + j] * conj(A[i * n + j]));
+                tot += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const cplx apq = A[p * n + q];
+                const double b = cabs(apq);
+                if (b == 0.0) continue;
+                /* rotate in the (p, q) plane: with u = apq / |apq|, the 2x2 block
+                   [[a, b u], [b conj(u), d]] is diagonalised by c, s with t = s / c solving
+                   t^2 + 2 zeta t - 1 = 0, zeta = (d - a) / (2 b) */
+                const double a = creal(A[p * n + p]), d = creal(A[q * n + q]);
+                const cplx u = apq / b;
+                const double zeta = (d - a) / (2.0 * b);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) { /* columns p, q */
+                    const cplx akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * conj(u) * akq;
+                    A[k * n + q] = s * u * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) { /* rows p, q */
+                    const cplx apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * u * aqk;
+                    A[q * n + k] = s * conj(u) * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const cplx zkp = Z[k * n + p], zkq = Z[k * n + q];
+                    Z[k * n + p] = c * zkp - s * conj(u) * zkq;
+                    Z[k * n + q] = s * u * zkp + c * zkq;
+                }
+            }
+    }
+    /* sort ascending (selection sort on the diagonal, columns of Z follow) */
+    for (int i = 0; i < n; ++i) ev[i] = creal(A[i * n + i]);
+    for (int i = 0; i < n; ++i) {
+        int m = i;
+        for (int j = i + 1; j < n; ++j)
+            if (ev[j] < ev[m]) m = j;
+        if (m != i) {
+            double t = ev[i];
+            ev[i] = ev[m];
+            ev[m] = t;
+            for (int k = 0; k < n; ++k) {
+                cplx z = Z[k * n + i];
+                Z[k * n + i] = Z[k * n + m];
+                Z[k * n + m] = z;
+            }
+        }
+    }
+}
+
+/* m-step Lanczos on H_w(mw)^2 from the start vector v0, with full re-orthogonalisation (classical
+ * Gram-Schmidt, twice), keeping the basis V [m][12V].  Returns the number of steps taken (fewer when
+ * the Krylov space closes). */
+static int lanczos_basis(const int *d, const double *bc, const cplx *U, double mw, int m, const cplx *v0, cplx *V)
+{
+    long N = 12 * volume(d);
+    cplx *w = malloc(sizeof(cplx) * N), *t = malloc(sizeof(cplx) * N);
+    double nr = sqrt(vnorm2(N, v0));
+    for (long k = 0; k < N; ++k) V[k] = v0[k] / nr;
+    int steps = m;
+    for (int j = 0; j < m; ++j) {
+        or_hw(d, bc, U, mw, V + (long)j * N, t);
+        or_hw(d, bc, U, mw, t, w);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i <= j; ++i) {
+                const cplx *vi = V + (long)i * N;
+                cplx h = vdot(N, vi, w);
+                for (long k = 0; k < N; ++k) w[k] -= h * vi[k];
+            }
+        double beta = sqrt(vnorm2(N, w));
+        if (j + 1 == m) break;
+        if (beta < 1e-13) {
+            steps = j + 1;
+            break;
+        }
+        for (long k = 0; k < N; ++k) V[(long)(j + 1) * N + k] = w[k] / beta;
+    }
+    free(w);
+    free(t);
+    return steps;
+}
+
+/* lambda_max estimate (Sec. II rescale, Eq. 5): the square root of the largest Ritz value of H_w^2
+ * from `steps` Lanczos steps started from v0 (a lower bound of the largest |eigenvalue| of H_w). */
+double or_lambda_max(const int *d, const double *bc, const cplx *U, double mw, int steps, const cplx *v0)
+{
+    init_gamma();
+    long N = 12 * volume(d);
+    cplx *V = malloc(sizeof(cplx) * N * steps), *w = malloc(sizeof(cplx) * N), *t = malloc(sizeof(cplx) * N);
+    int m = lanczos_basis(d, bc, U, mw, steps, v0, V);
+    /* Rayleigh-Ritz of H_w^2 in the basis: T_ij = v_i^dag H_w^2 v_j */
+    cplx *T = malloc(sizeof(cplx) * m * m), *Z = malloc(sizeof(cplx) * m * m);
+    double *ev = malloc(sizeof(double) * m);
+    for (int j = 0; j < m; ++j) {
+        or_hw(d, bc, U, mw, V + (long)j * N, t);
+        or_hw(d, bc, U, mw, t, w);
+        for (int i = 0; i < m; ++i) T[i * m + j] = vdot(N, V + (long)i * N, w);
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = i; j < m; ++j) {
+            cplx a = 0.5 * (T[i * m + j] + conj(T[j * m + i]));
+            T[i * m + j] = a;
+            T[j * m + i] = conj(a);
+        }
+    herm_jacobi(m, T, ev, Z);
+    double top = sqrt(ev[m - 1] > 0 ? ev[m - 1] : 0.0);
+    free(V);
+    free(w);
+    free(t);
+    free(T);
+    free(Z);
+    free(ev);
+    return top;
+}
+
+/* Rayleigh-Ritz of the Hermitian operator op on the orthonormal basis B [k][12V]: the k x k matrix
+ * B^dag op B, its eigenpairs (ascending) and the Ritz vectors out [k][12V] */
+static void rayleigh_ritz(const int *d, const double *bc, const cplx *U, double mw, int squared, int k,
+                          const cplx *B, double *ev, cplx *out)
+{
+    long N = 12 * volume(d);
+    cplx *w = malloc(sizeof(cplx) * N), *t = malloc(sizeof(cplx) * N);
+    cplx *T = malloc(sizeof(cplx) * k * k), *Z = malloc(sizeof(cplx) * k * k);
+    for (int j = 0; j < k; ++j) {
+        if (squared) {
+            or_hw(d, bc, U, mw, B + (long)j * N, t);
+            or_hw(d, bc, U, mw, t, w);
+        } else {
+            or_hw(d, bc, U, mw, B + (long)j * N, w);
+        }
+        for (int i = 0; i < k; ++i) T[i * k + j] = vdot(N, B + (long)i * N, w);
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = i; j < k; ++j) {
+            cplx a = 0.5 * (T[i * k + j] + conj(T[j * k + i]));
+            T[i * k + j] = a;
+            T[j * k + i] = conj(a);
+        }
+    herm_jacobi(k, T, ev, Z);
+    for (int i = 0; i < k; ++i) {
+        cplx *e = out + (long)i * N;
+        for (long q = 0; q < N; ++q) e[q] = 0;
+        for (int j = 0; j < k; ++j) {
+            const cplx z = Z[j * k + i];
+            const cplx *bj = B + (long)j * N;
+            for (long q = 0; q < N; ++q) e[q] += z * bj[q];
+        }
+    }
+    free(w);
+    free(t);
+    free(T);
+    free(Z);
+}
+
+/* The nev eigenpairs of H_w with smallest |lambda| (Sec. V: eigenvectors of H_w from a Krylov space of
+ * H_w^2): m Lanczos steps on H_w^2 from v0; Rayleigh-Ritz with H_w^2 on the basis (its smallest Ritz
+ * values are extremes of H_w^2, so they converge without spurious interior values); then Rayleigh-Ritz
+ * with H_w itself on the nev + 8 smallest of those Ritz vectors (a span that holds both partners of
+ * every +-lambda pair), which gives the signed lambda of Eq. 7.  vals [nev], vecs [nev][12V], sorted by
+ * |lambda|; returns the largest eigen-residual |H_w eta - lambda eta| of the returned pairs. */
+double or_lanczos_lowmodes(const int *d, const double *bc, const cplx *U, double mw, int m, int nev, const cplx *v0,
+                           double *vals, cplx *vecs)
+{
+    init_gamma();
+    long N = 12 * volume(d);
+    cplx *V = malloc(sizeof(cplx) * N * m), *w = malloc(sizeof(cplx) * N);
+    int mm = lanczos_basis(d, bc, U, mw, m, v0, V);
+    cplx *R2 = malloc(sizeof(cplx) * N * mm);
+    double *ev2 = malloc(sizeof(double) * mm);
+    rayleigh_ritz(d, bc, U, mw, 1, mm, V, ev2, R2);
+    int k = nev + 8 < mm ? nev + 8 : mm;
+    cplx *R1 = malloc(sizeof(cplx) * N * k);
+    double *ev1 = malloc(sizeof(double) * k);
+    rayleigh_ritz(d, bc, U, mw, 0, k, R2, ev1, R1);
+    int *o = malloc(sizeof(int) * k);
+    for (int i = 0; i < k; ++i) o[i] = i;
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j)
+            if (fabs(ev1[o[j]]) < fabs(ev1[o[i]])) {
+                int t = o[i];
+                o[i] = o[j];
+                o[j] = t;
+            }
+    double worst = 0;
+    for (int q = 0; q < nev && q < k; ++q) {
+        vals[q] = ev1[o[q]];
+        memcpy(vecs + (long)q * N, R1 + (long)o[q] * N, sizeof(cplx) * N);
+        or_hw(d, bc, U, mw, vecs + (long)q * N, w);
+        for (long i = 0; i < N; ++i) w[i] -= vals[q] * vecs[(long)q * N + i];
+        double r = sqrt(vnorm2(N, w));
+        if (r > worst) worst = r;
+    }
+    free(o);
+    free(V);
+    free(w);
+    free(R2);
+    free(ev2);
+    free(R1);
+    free(ev1);
+    return worst;
+}
+
+/* ------------------------------------------------------------------ */
 /* rational approximation, Eq. (12): Zolotarev's optimal P(x) ~ x^-1/2  */
 /* ------------------------------------------------------------------ */
 /* Complete elliptic integral K(m) of parameter m = k^2 (k the modulus), by the
