@@ -54,11 +54,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_sources_sha() -> str:
-    """Hash of the dslash kernel's sources: a DRAM-traffic figure from an ncu capture holds only
-    while the kernel it was taken on is unchanged."""
+VARIANT_UNIT = {0: "dslash_regs.cu", 1: "dslash_regs.cu", 2: "dslash_regs.cu", 3: "dslash_staged.cu",
+                4: "dslash_staged.cu", 5: "dslash_staged.cu", 6: "dslash_multi.cu", 7: "dslash_multi.cu",
+                8: "dslash_batched.cu", 9: "dslash_batched.cu", 10: "dslash_pair.cu", 11: "dslash_pair.cu"}
+
+
+def kernel_sources_sha(var: int = 1) -> str:
+    """Hash of the sources of the dslash kernel of launch variant `var`: a DRAM-traffic figure from
+    an ncu capture holds only while the kernel it was taken on is unchanged."""
     h = hashlib.sha256()
-    for f in ("dslash.cu", "ov_internal.cuh", "ov_kernels.h"):
+    for f in (VARIANT_UNIT[var], "dslash_common.cuh", "ov_internal.cuh", "ov_kernels.h"):
         with open(os.path.join(ROOT, "paper_1106_4964_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -67,11 +72,14 @@ def kernel_sources_sha() -> str:
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from the ncu captures
 # summarised under profiles/, keyed by (kernel, lattice, sources hash at capture time).  A kernel whose
 # sources changed since its capture gets null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # FP64, 1 rhs, block 256 x 1, register-budget variant 1 (the default run's timed kernel)
+    ("dslash_kernel<f64,f64,variant=1>", (24, 24, 24, 64), "3d6e9152e649c946"): 737_486_592 + 154_041_856,
+}
 
 
-def ncu_traffic(kernel: str):
-    return NCU_TRAFFIC.get((kernel, tuple(DIMS), kernel_sources_sha()))
+def ncu_traffic(kernel: str, var: int):
+    return NCU_TRAFFIC.get((kernel, tuple(DIMS), kernel_sources_sha(var)))
 
 
 def kernel_name(prec: str, var: int, nrhs: int = 1) -> str:
@@ -82,6 +90,10 @@ def kernel_name(prec: str, var: int, nrhs: int = 1) -> str:
         return f"dslash_tma_kernel<{prec},{prec},links_prefetched={var == 5}>"
     if var in (6, 7):
         return f"dslash_multi_kernel<{prec},{prec},rhs_per_thread={2 if var == 6 else 4}>"
+    if var in (8, 9):
+        return f"dslash_batched_kernel<{prec},{prec},hops_batched={4 if var == 8 else 8}>"
+    if var in (10, 11):
+        return f"dslash_pair_kernel<{prec},{prec},rhs_pairs_per_thread={1 if var == 10 else 2}>"
     return f"dslash_kernel<{prec},{prec},variant={var}>"
 
 
@@ -336,7 +348,7 @@ def run_gpu(args):
                        launches_per_step=reps),
         "GBps": round(gbs * world, 1),
         "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": fma_peak, "unit": "GFLOP/s",
-                     "frac": round(gflops / fma_peak, 4), "traffic": ncu_traffic(kern),
+                     "frac": round(gflops / fma_peak, 4), "traffic": ncu_traffic(kern, var),
                      "peak_kind": f"measured: {prec if prec in ('f64', 'f32') else 'f32'} FMA throughput of this "
                                   "GPU (ov_measure_fma_peak, same run)",
                      "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_nominal": round(gflops / FP64_NOMINAL_GFLOPS, 4),
@@ -359,10 +371,30 @@ def run_gpu(args):
         print(json.dumps(out))
 
 
+def sign_for_delta(ctx, eps, lmax, delta, degree):
+    """Install the Chebyshev sign on [eps, 1] with the lowest degree (a multiple of 10, at most 1000)
+    whose accuracy delta (Eq. 4, as the library evaluates it) is at most `delta`; a fixed `degree`
+    when delta is 0.  Returns (degree, delta)."""
+    if not delta > 0:
+        ctx.set_sign_poly(RHO, eps, degree, lmax)
+        return degree, ctx.get_option("sign_delta")
+    lo, hi = 1, 100  # bisection on multiples of 10: delta(10 lo) > target, delta(10 hi) <= target (or hi = 100)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        ctx.set_sign_poly(RHO, eps, 10 * mid, lmax)
+        if ctx.get_option("sign_delta") <= delta:
+            hi = mid
+        else:
+            lo = mid
+    ctx.set_sign_poly(RHO, eps, 10 * hi, lmax)
+    return 10 * hi, ctx.get_option("sign_delta")
+
+
 def propagator_record(args):
     """A small propagator at the paper's precision, inside the default run: the 12 spin-colour point
     sources on an 8^3 x 16 lattice (the same link generator), rho 1.5, the lowest 16 H_w modes deflated
-    in the sign (degree 100 on the rest) and the lowest 16 D^dag D modes deflating the CG, one
+    in the sign (on the rest, the lowest Chebyshev degree with delta <= 1e-10, the accuracy the paper
+    tunes its polynomial to) and the lowest 16 D^dag D modes deflating the CG, one
     multi-RHS mixed-precision CG (FP32 inner operator on the chiral sectors, FP64 true residuals and
     reliable updates) to the FP64 true residual 1e-10, quark mass --prop-mass.  Set-up (eigensolvers)
     is timed apart."""
@@ -383,7 +415,7 @@ def propagator_record(args):
     ctx.deflate(0, args.prop_nev, 1e-8)
     vals, _ = ctx.get_eigenpairs(0)
     eps = (0.99 * np.abs(vals).max() / lmax) ** 2
-    ctx.set_sign_poly(RHO, eps, 100, lmax)
+    degree, delta = sign_for_delta(ctx, eps, lmax, 1e-10, 0)
     setup["deflate_hw"] = time.perf_counter() - t0
     ctx.set_option("chiral", 1)
     t0 = time.perf_counter()
@@ -399,7 +431,7 @@ def propagator_record(args):
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     rec = {"workload": f"12 point sources, {dims[0]}^3x{dims[3]}, rho 1.5, mass {args.prop_mass}, {args.prop_nev} H_w + "
-                       f"{args.prop_nev} D^dag D modes, degree 100, eps {eps:.4g}",
+                       f"{args.prop_nev} D^dag D modes, degree {degree} (delta {delta:.2g}), eps {eps:.4g}",
            "solves_per_s": round(12 / t, 4), "propagators_per_s": round(1 / t, 5), "seconds": round(t, 3),
            "iterations": info["iterations"], "reliable_updates": info["reliable_updates"],
            "fallback": info["fallback"],
@@ -683,7 +715,7 @@ def run_propagator(args):
         setup["deflate_hw"] = time.perf_counter() - t0
         vals, _ = ctx.get_eigenpairs(0)
         eps = (0.99 * np.abs(vals).max() / lmax) ** 2
-    ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+    degree, delta = sign_for_delta(ctx, eps, lmax, args.sign_delta, args.degree)
     ctx.set_option("chiral", int(args.chiral))
     if args.nev_cg > 0:
         ctx.set_option("filter_dd", args.filter_dd)
@@ -746,8 +778,9 @@ def run_propagator(args):
         "dtype": f"mixed {args.cg_inner.replace(',', '/')} + {args.hi_prec}",
         "data": "synthetic",
         "config": {"workload": f"12 point sources, {dims[0]}^3x{dims[3]}, rho 1.5, mass {args.mass}, "
-                               f"{args.nev} H_w modes + {args.nev_cg} D^dag D modes, degree {args.degree}",
-                   "lattice": list(dims), "eps": eps, "lambda_max": lmax, "hi_prec": args.hi_prec,
+                               f"{args.nev} H_w modes + {args.nev_cg} D^dag D modes, degree {degree}",
+                   "lattice": list(dims), "eps": eps, "lambda_max": lmax, "sign_delta": delta,
+                   "hi_prec": args.hi_prec,
                    "chiral": bool(args.chiral)},
         "propagators_per_s": round(best["solves_per_s"] / 12, 5),
         "setup_s": {k: round(v, 1) for k, v in setup.items()}, "solves": out, "compare": compare,
@@ -781,7 +814,7 @@ def run_learned(args):
             ctx.deflate(0, args.nev, args.eig_tol)
             vals, _ = ctx.get_eigenpairs(0)
             eps = (0.99 * np.abs(vals).max() / lmax) ** 2
-        ctx.set_sign_poly(RHO, eps, args.degree, lmax)
+        sign_for_delta(ctx, eps, lmax, args.sign_delta, args.degree)
         if args.nev_cg > 0:
             ctx.set_option("filter_dd", args.filter_dd)
             ctx.deflate(1, args.nev_cg, args.eig_tol)
@@ -850,6 +883,8 @@ def main():
     ap.add_argument("--dims", type=int, nargs=4, default=None)
     ap.add_argument("--train-dims", type=int, nargs=4, default=[16, 16, 16, 32])
     ap.add_argument("--degree", type=int, default=200)
+    ap.add_argument("--sign-delta", type=float, default=1e-10,
+                    help="propagator / learned: lowest Chebyshev degree with this accuracy delta (0: --degree)")
     ap.add_argument("--nev", type=int, default=100)
     ap.add_argument("--nev-cg", type=int, default=100)
     ap.add_argument("--filter-dd", type=int, default=8)

@@ -72,7 +72,9 @@ typedef struct {
                                 one-sign chiral form was (two reliable updates in a row that did not
                                 halve the true residual), the solve continued with the two-sign operator */
     int nrhs;
-    double true_residual[64]; /* ||b - A x|| / ||b|| by the FP64 operator, per rhs */
+    double true_residual[64]; /* ||b - A x|| / ||b|| by the FP64 operator, per rhs; with exact
+                                 zero modes among the stored D^dag D modes (massless, excluded
+                                 from x) it is measured on their orthogonal complement */
     double seconds;          /* wall time of the solve */
 } ov_solve_info;
 
@@ -349,14 +351,25 @@ int ov_measure_fma_peak(int prec, double* gflops, void* stream);
  *                    of the full limit, writes nothing, and the call returns
  *                    OV_ETIMEOUT; a smaller value only tests that path. */
 int ov_set_option(ov_ctx* ctx, const char* name, double value);
-/* Current value of an option of ov_set_option, or "adaptive_degree": the
- * degree of the inner polynomial that "adaptive_delta" selected (the full
- * degree when it is off).  OV_EINVAL for an unknown name. */
+/* Current value of an option of ov_set_option, or one of two derived values:
+ * "adaptive_degree", the degree of the inner polynomial that "adaptive_delta"
+ * selected (the full degree when it is off); "sign_delta", the accuracy
+ * delta = max |1 - sqrt(x) P(x)| over [eps, 1] (Eq. 4) of the installed sign
+ * approximation (sampled at 4001 points for the polynomial, Zolotarev's
+ * closed form for the rational one; OV_ESTATE before any).  OV_EINVAL for an
+ * unknown name. */
 int ov_get_option(const ov_ctx* ctx, const char* name, double* value);
 /* Launch configuration of the dslash for (prec, nrhs): block = bx sites x by
- * right-hand sides, and a register-budget variant (0: unbounded; 1, 2:
- * registers capped so that more warps are resident).  ov_tune_dslash times
- * every candidate on `stream` and keeps the fastest (the autotuner). */
+ * right-hand sides, and a kernel variant: 0 unbounded registers; 1, 2
+ * registers capped so that more warps are resident; 3 neighbours staged in
+ * shared memory by cp.async; 4, 5 staged by bulk copies (bx = 128, by = 1);
+ * 6, 7 two or four right-hand sides per thread sharing each link; 8, 9 the
+ * loads of four or eight hops issued before their arithmetic (by = 1); 10, 11
+ * two or four right-hand sides per thread as pairs on the packed FP32 pipe
+ * (for 6, 7, 10, 11 `by` counts groups of right-hand sides and bx * by <=
+ * 128).  Variants 3-11 take FP32 arithmetic (FP32 and 16-bit storage) only.
+ * ov_tune_dslash times every candidate on `stream` and keeps the fastest
+ * (the autotuner). */
 int ov_set_dslash_shape(ov_ctx* ctx, int prec, int nrhs, int bx, int by, int variant);
 int ov_tune_dslash(ov_ctx* ctx, int prec, int nrhs, int* bx, int* by, int* variant, void* stream);
 

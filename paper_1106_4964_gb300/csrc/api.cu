@@ -1376,6 +1376,11 @@ int ov_get_option(const ov_ctx* c, const char* name, double* value)
     else if (n == "rational_tol") *value = c->rational_tol;
     else if (n == "rational_iterations") *value = (double)c->rational_iters;
     else if (n == "adaptive_degree") *value = c->degree_in;
+    else if (n == "sign_delta") {
+        if (c->sign_backend == 1) *value = c->rdelta;
+        else if (c->coef.empty()) return OV_ESTATE;
+        else *value = poly_delta(c->coef, c->eps);
+    }
     else return OV_EINVAL;
     return OV_OK;
 }
@@ -1396,7 +1401,7 @@ int ov_set_dslash_shape(ov_ctx* c, int prec, int nrhs, int bx, int by, int varia
         ((variant == 3 || variant == 4 || variant == 5) && by != 1))
         return set_err(c, OV_EINVAL, "bad variant %d for this precision / shape", variant);
     const int maxt = variant == 0 ? (wide(prec) ? 256 : 512) : (variant == 3 || variant >= 6 ? 128 : 256);
-    if (variant >= 8 && by != 1) return set_err(c, OV_EINVAL, "variants 8, 9: by must be 1");
+    if ((variant == 8 || variant == 9) && by != 1) return set_err(c, OV_EINVAL, "variants 8, 9: by must be 1");
     if (bx < 1 || by < 1 || bx * by > maxt || bx % 32) return set_err(c, OV_EINVAL, "bad shape %d x %d", bx, by);
     c->shape[{prec, nrhs}] = std::make_tuple(bx, by, variant);
     return OV_OK;
@@ -1427,7 +1432,7 @@ int ov_tune_dslash(ov_ctx* c, int prec, int nrhs, int* bx, int* by, int* variant
             continue;
         }
         if (v >= 6) {                        // 2 or 4 right-hand sides per thread
-            const int rb = v == 6 ? 2 : 4;
+            const int rb = (v == 6 || v == 10) ? 2 : 4;
             if (nrhs < rb) continue;
             const int groups = (nrhs + rb - 1) / rb;
             for (int x : {32, 64, 128})

@@ -1,1072 +1,20 @@
-// Even/odd Wilson dslash on the internal layout (Eqs. 1-2 of the paper):
-//
-//   D_w(m) psi(n) = (m + 4) psi(n)
-//                 - 1/2 sum_mu [ U_mu(n) (1 - gamma_mu) psi(n + mu)
-//                              + U_mu(n - mu)^dag (1 + gamma_mu) psi(n - mu) ]
-//
-// One launch computes both parities of the output: block b handles parity
-// b & 1 and checkerboard sites [(b >> 1) * BX, +BX), so the two parities of
-// the same region run together and the links and neighbour spinors one
-// parity reads are re-read by the other while they sit in L2.  Threads
-// (x, y) of a block handle site x of right-hand side blockIdx.y*BY + y; the
-// BY right-hand sides of a block share every link load through L1.
-//
-// Spin structure (Euclidean chiral basis, gamma_mu = [[0, A_mu], [A_mu^dag, 0]],
-// A_k = -i sigma_k, A_4 = 1): (1 - S gamma_mu) psi has upper half
-// h = psi_up - S A_mu psi_dn and lower half -S A_mu^dag h, so each hop
-// projects to a 2-spin half spinor, multiplies it by the link and
-// reconstructs the lower half (S = +1 forward, -1 backward).
-//
-// Generic epilogue:
-//   core = a * psi(n) + b * hop_sum;  core = gamma5 core if g5_core
-//   out  = core + sum_j sy[j] * y_j(n);  out = gamma5 out if g5_out
-// which gives D_w (a = 4+m, b = -1/2), H_w (g5_core), and the fused
-// Clenshaw step b_k = c_k psi_h + alpha H_w t + beta b_{k+1} - b_{k+2}.
-#include <type_traits>
-
+// Wilson dslash launch: validates the launch configuration and hands it to the translation unit
+// that holds the chosen variant (the kernels and their layout are described in dslash_common.cuh).
 #include "ov_internal.cuh"
 #include "ov_kernels.h"
 
 namespace ov {
 
-namespace {
-
-template <int SP>
-using real_t = typename std::conditional<SP == P_F64, double, typename std::conditional<SP == P_DF64, df64, float>::type>::type;
-template <int SP>
-constexpr bool wide_dev = SP == P_F64 || SP == P_DF64;
-
-template <int MU, int S, typename Real>
-__device__ __forceinline__ void project(const Real v[24], Real h[12])
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Real u0r = v[2 * (0 + c)], u0i = v[2 * (0 + c) + 1];
-        Real u1r = v[2 * (3 + c)], u1i = v[2 * (3 + c) + 1];
-        Real d0r = v[2 * (6 + c)], d0i = v[2 * (6 + c) + 1];
-        Real d1r = v[2 * (9 + c)], d1i = v[2 * (9 + c) + 1];
-        Real a0r, a0i, a1r, a1i;  // (A_mu psi_dn)_{0,1}
-        if constexpr (MU == 0) {  // A = [[0,-i],[-i,0]]
-            a0r = d1i; a0i = -d1r;
-            a1r = d0i; a1i = -d0r;
-        } else if constexpr (MU == 1) {  // A = [[0,-1],[1,0]]
-            a0r = -d1r; a0i = -d1i;
-            a1r = d0r; a1i = d0i;
-        } else if constexpr (MU == 2) {  // A = diag(-i, i)
-            a0r = d0i; a0i = -d0r;
-            a1r = -d1i; a1i = d1r;
-        } else {  // A = 1
-            a0r = d0r; a0i = d0i;
-            a1r = d1r; a1i = d1i;
-        }
-        h[2 * c] = u0r - S * a0r;
-        h[2 * c + 1] = u0i - S * a0i;
-        h[6 + 2 * c] = u1r - S * a1r;
-        h[6 + 2 * c + 1] = u1i - S * a1i;
-    }
-}
-
-template <int MU, int S, typename Real>
-__device__ __forceinline__ void accumulate(Real acc[24], const Real chi[12])
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Real x0r = chi[2 * c], x0i = chi[2 * c + 1];
-        Real x1r = chi[6 + 2 * c], x1i = chi[6 + 2 * c + 1];
-        acc[2 * (0 + c)] += x0r;
-        acc[2 * (0 + c) + 1] += x0i;
-        acc[2 * (3 + c)] += x1r;
-        acc[2 * (3 + c) + 1] += x1i;
-        Real b0r, b0i, b1r, b1i;  // (A_mu^dag chi)_{0,1}
-        if constexpr (MU == 0) {  // A^dag = [[0,i],[i,0]]
-            b0r = -x1i; b0i = x1r;
-            b1r = -x0i; b1i = x0r;
-        } else if constexpr (MU == 1) {  // A^dag = [[0,1],[-1,0]]
-            b0r = x1r; b0i = x1i;
-            b1r = -x0r; b1i = -x0i;
-        } else if constexpr (MU == 2) {  // A^dag = diag(i, -i)
-            b0r = -x0i; b0i = x0r;
-            b1r = x1i; b1i = -x1r;
-        } else {
-            b0r = x0r; b0i = x0i;
-            b1r = x1r; b1i = x1i;
-        }
-        acc[2 * (6 + c)] -= S * b0r;
-        acc[2 * (6 + c) + 1] -= S * b0i;
-        acc[2 * (9 + c)] -= S * b1r;
-        acc[2 * (9 + c) + 1] -= S * b1i;
-    }
-}
-
-// a * b + c as one fused multiply-add (FP32, FP64); double-float composes its own operations
-template <typename Real>
-__device__ __forceinline__ Real fmac(Real a, Real b, Real c)
-{
-    if constexpr (std::is_same<Real, df64>::value)
-        return a * b + c;
-    else
-        return fma(a, b, c);
-}
-
-// chi = U h (forward) or U^dag h (backward), two spins.  Each real part is one chain of fused
-// multiply-adds, 6 per component (the form re += ur*hr - ui*hi would cost a multiply, a fused
-// multiply-add and an add per term: 108 instead of 72 operations per hop)
-template <int S, typename Real>
-__device__ __forceinline__ void link_mul(const Real u[18], const Real h[12], Real chi[12])
-{
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            Real re, im;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Real ur, ui;  // U_ij, or conj(U_ji) for the backward hop
-                if constexpr (S > 0) {
-                    ur = u[2 * (3 * i + j)];
-                    ui = u[2 * (3 * i + j) + 1];
-                } else {
-                    ur = u[2 * (3 * j + i)];
-                    ui = -u[2 * (3 * j + i) + 1];
-                }
-                const Real hr = h[6 * a + 2 * j], hi = h[6 * a + 2 * j + 1];
-                if (j == 0) {
-                    re = ur * hr;
-                    im = ur * hi;
-                } else {
-                    re = fmac<Real>(ur, hr, re);
-                    im = fmac<Real>(ur, hi, im);
-                }
-                re = fmac<Real>(-ui, hi, re);
-                im = fmac<Real>(ui, hr, im);
-            }
-            chi[6 * a + 2 * i] = re;
-            chi[6 * a + 2 * i + 1] = im;
-        }
-    }
-}
-
-template <int SP, int GP, int MU, int S>
-__device__ __forceinline__ void hop(const DslashArgs& A, const char* in_q, const float* inn_q, int p, int s, int sn,
-                                    bool cross, real_t<SP> acc[24])
-{
-    using Real = real_t<SP>;
-    Real v[24];
-    Real h[12];
-    if constexpr (SP == P_F16 || SP == P_BF16) {
-        // 16-bit storage: project the unscaled values and apply the site's scale (and the boundary
-        // phase) to the 12 projected reals instead of the 24 loaded ones
-        float n = load_spinor_unscaled<SP>(in_q, inn_q, A.g.Vh, sn, v);
-        project<MU, S, Real>(v, h);
-        if (cross) n *= A.g.fbc[MU];
-#pragma unroll
-        for (int i = 0; i < 12; ++i) h[i] *= n;
-    } else {
-        load_spinor<SP, Real>(in_q, inn_q, A.g.Vh, sn, v);
-        project<MU, S, Real>(v, h);
-        if (cross) {
-            const Real ph = coef<Real>(A.g.bc[MU], A.g.fbc[MU]);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) h[i] *= ph;
-        }
-    }
-    const int lpar = S > 0 ? p : 1 - p;
-    const int ls = S > 0 ? s : sn;
-    const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
-    Real u[18];
-    load_link<GP, Real>(lb, A.g.Vh, ls, u);
-    Real chi[12];
-    link_mul<S, Real>(u, h, chi);
-    accumulate<MU, S, Real>(acc, chi);
-}
-
-template <int SP, int NY>
-__device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int s, const real_t<SP> acc[24]);
-
-// Register-budget variants chosen by the autotuner: VAR 0 lets the compiler
-// use what it wants (low occupancy, long latency chains), VAR 1 and 2 cap
-// the registers so that more warps are resident to hide load latency.
-template <int SP, int VAR>
-struct Bounds {
-    static constexpr int maxt = VAR == 0 ? (wide_dev<SP> ? 256 : 512) : 256;
-    static constexpr int minb = VAR == 0 ? 1 : (wide_dev<SP> ? VAR + 1 : VAR + 2);
-};
-
-template <int SP, int GP, int NY, int VAR>
-__global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) dslash_kernel(DslashArgs A)
-{
-    using Real = real_t<SP>;
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    const Geom& g = A.g;
-    if (s >= g.Vh || r >= A.nrhs) return;
-
-    constexpr size_t CH = nchunk_dev<SP>() * 16;
-    const size_t par_bytes = CH * g.Vh;
-    const int q = 1 - p;
-    const char* in_q = A.in + ((size_t)r * 2 + q) * par_bytes;
-    const float* inn_q = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
-
-    int c[4];
-    cb_coords(g, s, p, c);
-    Real acc[24];
-#pragma unroll
-    for (int i = 0; i < 24; ++i) acc[i] = 0;
-
-    // neighbour index computed at its hop (short live ranges); the flag marks a boundary crossing
-    hop<SP, GP, 0, +1>(A, in_q, inn_q, p, s, cb_neighbour<0>(g, s, c), c[0] + 1 == g.L[0], acc);
-    hop<SP, GP, 0, -1>(A, in_q, inn_q, p, s, cb_neighbour<1>(g, s, c), c[0] == 0, acc);
-    hop<SP, GP, 1, +1>(A, in_q, inn_q, p, s, cb_neighbour<2>(g, s, c), c[1] + 1 == g.L[1], acc);
-    hop<SP, GP, 1, -1>(A, in_q, inn_q, p, s, cb_neighbour<3>(g, s, c), c[1] == 0, acc);
-    hop<SP, GP, 2, +1>(A, in_q, inn_q, p, s, cb_neighbour<4>(g, s, c), c[2] + 1 == g.L[2], acc);
-    hop<SP, GP, 2, -1>(A, in_q, inn_q, p, s, cb_neighbour<5>(g, s, c), c[2] == 0, acc);
-    hop<SP, GP, 3, +1>(A, in_q, inn_q, p, s, cb_neighbour<6>(g, s, c), c[3] + 1 == g.L[3], acc);
-    hop<SP, GP, 3, -1>(A, in_q, inn_q, p, s, cb_neighbour<7>(g, s, c), c[3] == 0, acc);
-
-    epilogue<SP, NY>(A, r, p, s, acc);
-}
-
-// out(n) = g5_out[ g5_core(a psi(n) + b acc) + sum_j sy_j y_j(n) ], stored in the field format
-template <int SP, int NY>
-__device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int s, const real_t<SP> acc[24])
-{
-    using Real = real_t<SP>;
-    const Geom& g = A.g;
-    constexpr size_t CH = nchunk_dev<SP>() * 16;
-    const size_t par_bytes = CH * g.Vh;
-    const size_t off = ((size_t)r * 2 + p) * par_bytes;
-    const size_t noff = ((size_t)r * 2 + p) * g.Vh;
-    Real o[24];
-    {
-        Real self[24];
-        load_spinor<SP, Real>(A.in + off, A.in_n ? A.in_n + noff : nullptr, g.Vh, s, self);
-        const Real a = coef<Real>(A.a, A.fa), b = coef<Real>(A.b, A.fb);
-#pragma unroll
-        for (int i = 0; i < 24; ++i) o[i] = a * self[i] + b * acc[i];
-    }
-    if (A.g5_core) {
-#pragma unroll
-        for (int i = 12; i < 24; ++i) o[i] = -o[i];
-    }
-#pragma unroll
-    for (int j = 0; j < NY; ++j) {
-        Real w[24];
-        load_spinor<SP, Real>(A.y[j] + off, A.y_n[j] ? A.y_n[j] + noff : nullptr, g.Vh, s, w);
-        const Real sj = coef<Real>(A.sy[j], A.fsy[j]);
-#pragma unroll
-        for (int i = 0; i < 24; ++i) o[i] += sj * w[i];
-    }
-    if (A.g5_out) {
-#pragma unroll
-        for (int i = 12; i < 24; ++i) o[i] = -o[i];
-    }
-    store_spinor<SP, Real>(A.out + off, A.out_n ? A.out_n + noff : nullptr, g.Vh, s, o);
-}
-
-// ---------------------------------------------------------------------------
-// Variant 3 (FP32 arithmetic only): every thread stages the 8 neighbour
-// spinors and links of its site into its own shared-memory slots with
-// cp.async, one commit group per hop, so all of a site's loads are in flight
-// at once without occupying registers; hop h then waits only for group h.
-// Slots are chunk-major ([hop][chunk][thread]) so a warp's accesses hit
-// consecutive 16-byte words.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-template <int SP, int GP>
-struct AsyncLayout {
-    static constexpr int SCH = nchunk_dev<SP>();                  // 16-byte spinor chunks
-    static constexpr int LCB = GP == P_F32 ? 16 : 8;              // bytes of each of the 3 link chunks
-    static constexpr int NRM = (SP == P_F16 || SP == P_BF16) ? 4 : 0;
-    static constexpr int PER_THREAD = 8 * (SCH * 16 + 3 * LCB + NRM);
-    __device__ static uint8_t* spin(uint8_t* sm, int BX, int h, int k, int t) { return sm + ((h * SCH + k) * BX + t) * 16; }
-    __device__ static uint8_t* link(uint8_t* sm, int BX, int h, int k, int t)
-    {
-        return sm + 8 * SCH * 16 * BX + ((h * 3 + k) * BX + t) * LCB;
-    }
-    __device__ static uint8_t* norm(uint8_t* sm, int BX, int h, int t)
-    {
-        return sm + 8 * (SCH * 16 + 3 * LCB) * BX + (h * BX + t) * 4;
-    }
-};
-
-template <int SP, int GP>
-__device__ __forceinline__ void stage_hop(uint8_t* sm, int BX, int t, int h, const char* in_q, const float* inn_q,
-                                          int Vh, int sn, const char* lbase, int ls)
-{
-    using L = AsyncLayout<SP, GP>;
-#pragma unroll
-    for (int k = 0; k < L::SCH; ++k) cp_async16(L::spin(sm, BX, h, k, t), in_q + ((size_t)k * Vh + sn) * 16);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if constexpr (L::LCB == 16)
-            cp_async16(L::link(sm, BX, h, k, t), lbase + ((size_t)k * Vh + ls) * 16);
-        else
-            cp_async8(L::link(sm, BX, h, k, t), lbase + ((size_t)k * Vh + ls) * 8);
-    }
-    if constexpr (L::NRM) cp_async4(L::norm(sm, BX, h, t), inn_q + sn);
-    cp_async_commit();
-}
-
-template <int SP, int GP, int MU, int S, int H>
-__device__ __forceinline__ void hop_staged(uint8_t* sm, int BX, int t, bool cross, float phase, float acc[24])
-{
-    using L = AsyncLayout<SP, GP>;
-    cp_async_wait<7 - H>();
-    float v[24];
-    if constexpr (SP == P_F32) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(L::spin(sm, BX, H, k, t));
-            v[4 * k] = a.x;
-            v[4 * k + 1] = a.y;
-            v[4 * k + 2] = a.z;
-            v[4 * k + 3] = a.w;
-        }
-    } else {
-        const float n = *reinterpret_cast<const float*>(L::norm(sm, BX, H, t));
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint4 a = *reinterpret_cast<const uint4*>(L::spin(sm, BX, H, k, t));
-            const float2 a0 = Half<SP>::to2(a.x), a1 = Half<SP>::to2(a.y), a2 = Half<SP>::to2(a.z),
-                         a3 = Half<SP>::to2(a.w);
-            v[8 * k + 0] = a0.x * n;
-            v[8 * k + 1] = a0.y * n;
-            v[8 * k + 2] = a1.x * n;
-            v[8 * k + 3] = a1.y * n;
-            v[8 * k + 4] = a2.x * n;
-            v[8 * k + 5] = a2.y * n;
-            v[8 * k + 6] = a3.x * n;
-            v[8 * k + 7] = a3.y * n;
-        }
-    }
-    float h[12];
-    project<MU, S, float>(v, h);
-    if (cross) {
-#pragma unroll
-        for (int i = 0; i < 12; ++i) h[i] *= phase;
-    }
-    float u[18];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if constexpr (GP == P_F32) {
-            const float4 a = *reinterpret_cast<const float4*>(L::link(sm, BX, H, k, t));
-            u[4 * k] = a.x;
-            u[4 * k + 1] = a.y;
-            u[4 * k + 2] = a.z;
-            u[4 * k + 3] = a.w;
-        } else {
-            const uint2 a = *reinterpret_cast<const uint2*>(L::link(sm, BX, H, k, t));
-            const float2 a0 = Half<GP>::to2(a.x), a1 = Half<GP>::to2(a.y);
-            u[4 * k] = a0.x;
-            u[4 * k + 1] = a0.y;
-            u[4 * k + 2] = a1.x;
-            u[4 * k + 3] = a1.y;
-        }
-    }
-    link_row2<float>(u);  // row 2 = conj(row0 x row1)
-    float chi[12];
-    link_mul<S, float>(u, h, chi);
-    accumulate<MU, S, float>(acc, chi);
-}
-
-template <int SP, int GP, int NY>
-__global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
-{
-    extern __shared__ __align__(16) uint8_t sm[];
-    const int BX = blockDim.x, tx = threadIdx.x;
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * BX + tx;
-    const int r = blockIdx.y;
-    const Geom& g = A.g;
-    if (s >= g.Vh || r >= A.nrhs) return;
-    constexpr size_t CH = nchunk_dev<SP>() * 16;
-    const size_t par_bytes = CH * g.Vh;
-    const int q = 1 - p;
-    const char* in_q = A.in + ((size_t)r * 2 + q) * par_bytes;
-    const float* inn_q = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
-    int c[4];
-    cb_coords(g, s, p, c);
-    int nbr[8];
-    cb_neighbours(g, s, c, nbr);
-    // hops crossing the lattice boundary (they carry the boundary phase)
-    const bool xp0 = c[0] + 1 == g.L[0], xm0 = c[0] == 0, yp0 = c[1] + 1 == g.L[1], ym0 = c[1] == 0;
-    const bool zp0 = c[2] + 1 == g.L[2], zm0 = c[2] == 0, tp0 = c[3] + 1 == g.L[3], tm0 = c[3] == 0;
-    const int* sn = nbr;
-    constexpr size_t LB = gauge_link_bytes_dev<GP>();
-#pragma unroll
-    for (int h = 0; h < 8; ++h) {
-        const int mu = h >> 1;
-        const bool fwd = (h & 1) == 0;
-        const int lpar = fwd ? p : q, ls = fwd ? s : sn[h];
-        stage_hop<SP, GP>(sm, BX, tx, h, in_q, inn_q, g.Vh, sn[h], A.gauge + ((size_t)(lpar * 4 + mu) * g.Vh) * LB, ls);
-    }
-    float acc[24];
-#pragma unroll
-    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_staged<SP, GP, 0, +1, 0>(sm, BX, tx, xp0, g.fbc[0], acc);
-    hop_staged<SP, GP, 0, -1, 1>(sm, BX, tx, xm0, g.fbc[0], acc);
-    hop_staged<SP, GP, 1, +1, 2>(sm, BX, tx, yp0, g.fbc[1], acc);
-    hop_staged<SP, GP, 1, -1, 3>(sm, BX, tx, ym0, g.fbc[1], acc);
-    hop_staged<SP, GP, 2, +1, 4>(sm, BX, tx, zp0, g.fbc[2], acc);
-    hop_staged<SP, GP, 2, -1, 5>(sm, BX, tx, zm0, g.fbc[2], acc);
-    hop_staged<SP, GP, 3, +1, 6>(sm, BX, tx, tp0, g.fbc[3], acc);
-    hop_staged<SP, GP, 3, -1, 7>(sm, BX, tx, tm0, g.fbc[3], acc);
-    epilogue<SP, NY>(A, r, p, s, acc);
-}
-
-template <int SP, int GP>
-cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
-{
-    if constexpr (wide_dev<SP>) {
-        return cudaErrorInvalidValue;
-    } else {
-        if (block.y != 1 || block.x > 128) return cudaErrorInvalidValue;
-        const size_t shm = (size_t)block.x * AsyncLayout<SP, GP>::PER_THREAD;
-        static bool attr_set[4] = {false, false, false, false};
-        if (!attr_set[ny]) {
-            cudaError_t e = cudaSuccess;
-            switch (ny) {
-            case 0: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
-            case 1: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
-            case 2: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
-            case 3: e = cudaFuncSetAttribute(dslash_staged_kernel<SP, GP, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); break;
-            default: return cudaErrorInvalidValue;
-            }
-            if (e != cudaSuccess) return e;
-            attr_set[ny] = true;
-        }
-        dim3 g2(grid.x, A.nrhs);
-        switch (ny) {
-        case 0: dslash_staged_kernel<SP, GP, 0><<<g2, block, shm, st>>>(A); break;
-        case 1: dslash_staged_kernel<SP, GP, 1><<<g2, block, shm, st>>>(A); break;
-        case 2: dslash_staged_kernel<SP, GP, 2><<<g2, block, shm, st>>>(A); break;
-        case 3: dslash_staged_kernel<SP, GP, 3><<<g2, block, shm, st>>>(A); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Variant 4 (FP32 arithmetic, FP32 or 16-bit storage): neighbour spinors
-// staged in shared memory by the bulk-copy engine (1-D TMA).  A block owns
-// TB consecutive checkerboard sites [s0, s0 + TB) of one parity and one
-// right-hand side; the neighbours of the other parity lie in five index
-// ranges, [s0 - Lxh - 1, s0 + TB + Lxh + 1) for the x and y hops and the
-// ranges shifted by +-Lxh Ly (z hops) and +-Lxh Ly Lz (t hops).  Thread 0
-// issues one cp.async.bulk per (range, chunk) plus the per-site scales of
-// 16-bit storage, all completing on one mbarrier; a hop whose neighbour lies
-// outside its range (lattice wrap-around, clipped array ends) reads global
-// memory instead.  Links have no reuse within a parity and stay plain loads.
-// Blocks are ordered (site block, parity, rhs) with the rhs fastest, so the
-// right-hand sides of one site block read the same links back to back (L2).
-// ---------------------------------------------------------------------------
-constexpr int TMA_TB = 128;                 // sites per block
-constexpr long long TMA_SPIN = 1ll << 22;   // bounded mbarrier wait (polls; also 2 s of wall time)
-
-struct TmaPlan {
-    int cap[5];        // slots per range
-    int spin_off[5];   // byte offsets of the spinor slots
-    int nrm_off[5];    // byte offsets of the scale slots (16-bit storage)
-    int bytes;         // dynamic shared memory
-};
-
-__host__ __device__ inline TmaPlan tma_plan(int Lxh, int nch, bool nrm)
-{
-    TmaPlan P;
-    int off = 16;  // the mbarrier
-    for (int j = 0; j < 5; ++j) {
-        P.cap[j] = j == 0 ? TMA_TB + 2 * Lxh + 2 : TMA_TB;
-        P.spin_off[j] = off;
-        off += nch * P.cap[j] * 16;
-    }
-    for (int j = 0; j < 5; ++j) {
-        P.nrm_off[j] = off;
-        if (nrm) off += ((P.cap[j] + 8) * 4 + 15) & ~15;
-    }
-    P.bytes = off;
-    return P;
-}
-
-__device__ __forceinline__ void tma_mbar_init(uint64_t* b)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void tma_expect(uint64_t* b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool tma_wait(uint64_t* b, long long polls)
-{
-    const unsigned long long t0 = global_ns();
-    for (long long i = 0; i < polls; ++i) {
-        if ((i & 1023) == 1023 && global_ns() - t0 > WAIT_LIMIT_NS) return false;
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_addr(b))
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// spinor of slot i of a staged range (chunk-major, `cap` slots per chunk)
-template <int SP>
-__device__ __forceinline__ void load_spinor_smem(const uint8_t* base, const float* nrm, int cap, int i, float v[24])
-{
-    if constexpr (SP == P_F32) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float4 a = *reinterpret_cast<const float4*>(base + ((size_t)k * cap + i) * 16);
-            v[4 * k] = a.x;
-            v[4 * k + 1] = a.y;
-            v[4 * k + 2] = a.z;
-            v[4 * k + 3] = a.w;
-        }
-    } else {
-        const float n = *nrm;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint4 a = *reinterpret_cast<const uint4*>(base + ((size_t)k * cap + i) * 16);
-            const float2 a0 = Half<SP>::to2(a.x), a1 = Half<SP>::to2(a.y), a2 = Half<SP>::to2(a.z),
-                         a3 = Half<SP>::to2(a.w);
-            v[8 * k + 0] = a0.x * n;
-            v[8 * k + 1] = a0.y * n;
-            v[8 * k + 2] = a1.x * n;
-            v[8 * k + 3] = a1.y * n;
-            v[8 * k + 4] = a2.x * n;
-            v[8 * k + 5] = a2.y * n;
-            v[8 * k + 6] = a3.x * n;
-            v[8 * k + 7] = a3.y * n;
-        }
-    }
-}
-
-struct TmaRange {
-    int a, n, na;  // first staged index, count, first staged scale index
-};
-
-// lk: rows 0-1 of the hop's link, loaded before the wait (PRE), else loaded here
-template <int SP, int GP, int MU, int S, bool PRE>
-__device__ __forceinline__ void hop_tma(const DslashArgs& A, const uint8_t* sm, const TmaPlan& P, const TmaRange& rg,
-                                        int j, const char* in_q, const float* inn_q, int p, int s, int sn, bool cross,
-                                        const float* lk, float acc[24])
-{
-    float v[24];
-    const int i = sn - rg.a;
-    if ((unsigned)i < (unsigned)rg.n) {
-        const float* nrm = nullptr;
-        if constexpr (SP == P_F16 || SP == P_BF16)
-            nrm = reinterpret_cast<const float*>(sm + P.nrm_off[j]) + (sn - rg.na);
-        load_spinor_smem<SP>(sm + P.spin_off[j], nrm, P.cap[j], i, v);
-    } else {
-        load_spinor<SP, float>(in_q, inn_q, A.g.Vh, sn, v);
-    }
-    float h[12];
-    project<MU, S, float>(v, h);
-    if (cross) {
-        const float ph = A.g.fbc[MU];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) h[k] *= ph;
-    }
-    float u[18];
-    if constexpr (PRE) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) u[k] = lk[k];
-        link_row2<float>(u);
-    } else {
-        const int lpar = S > 0 ? p : 1 - p;
-        const int ls = S > 0 ? s : sn;
-        const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
-        load_link<GP, float>(lb, A.g.Vh, ls, u);
-    }
-    float chi[12];
-    link_mul<S, float>(u, h, chi);
-    accumulate<MU, S, float>(acc, chi);
-}
-
-template <int GP>
-__device__ __forceinline__ void prefetch_link(const DslashArgs& A, int lpar, int mu, int ls, float w[12])
-{
-    const char* lb = A.gauge + ((size_t)(lpar * 4 + mu) * A.g.Vh) * gauge_link_bytes_dev<GP>();
-    float u[18];
-    load_link_rows<GP, float>(lb, A.g.Vh, ls, u);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) w[k] = u[k];
-}
-
-// PRE: every thread loads the rows of its eight links while the bulk copies are in flight
-template <int SP, int GP, int NY, bool PRE>
-__global__ void __launch_bounds__(TMA_TB, PRE ? 3 : 1) dslash_tma_kernel(DslashArgs A)
-{
-    extern __shared__ __align__(16) uint8_t sm[];  // bulk copies need 16-byte alignment
-    constexpr int SCH = nchunk_dev<SP>();
-    constexpr bool NRM = SP == P_F16 || SP == P_BF16;
-    const Geom& g = A.g;
-    const int r = blockIdx.x % A.nrhs;
-    const int rest = blockIdx.x / A.nrhs;
-    const int p = rest & 1, q = 1 - p;
-    const int s0 = (rest >> 1) * TMA_TB;
-    const char* in_q = A.in + ((size_t)r * 2 + q) * SCH * 16 * g.Vh;
-    const float* inn_q = NRM ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
-    const TmaPlan P = tma_plan(g.Lxh, SCH, NRM);
-    const int PL = g.Lxh * g.L[1], VL = PL * g.L[2];
-    const int lo[5] = {s0 - g.Lxh - 1, s0 + PL, s0 - PL, s0 + VL, s0 - VL};
-    TmaRange rg[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const int a = lo[j] < 0 ? 0 : lo[j];
-        const int e = lo[j] + P.cap[j] > g.Vh ? g.Vh : lo[j] + P.cap[j];
-        rg[j].a = a;
-        rg[j].n = e > a ? e - a : 0;
-        rg[j].na = a & ~3;
-    }
-    const int s = s0 + threadIdx.x;
-    int c[4] = {0, 0, 0, 0};
-    if (s < g.Vh) cb_coords(g, s, p, c);
-    int nbr[8];
-    cb_neighbours(g, s, c, nbr);
-    // hops crossing the lattice boundary (they carry the boundary phase)
-    const bool xp0 = c[0] + 1 == g.L[0], xm0 = c[0] == 0, yp0 = c[1] + 1 == g.L[1], ym0 = c[1] == 0;
-    const bool zp0 = c[2] + 1 == g.L[2], zm0 = c[2] == 0, tp0 = c[3] + 1 == g.L[3], tm0 = c[3] == 0;
-    const int* nb = nbr;
-    float lk[PRE ? 8 : 1][12];
-    if constexpr (PRE) {
-        if (s < g.Vh) {
-#pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                const int mu = h >> 1;
-                const bool fwd = (h & 1) == 0;
-                prefetch_link<GP>(A, fwd ? p : q, mu, fwd ? s : nb[h], lk[h]);
-            }
-        }
-    }
-
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
-    if (threadIdx.x == 0) tma_mbar_init(bar);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t total = 0;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            if (rg[j].n == 0) continue;
-            total += SCH * rg[j].n * 16;
-            if (NRM) total += ((((rg[j].a + rg[j].n + 3) & ~3) - rg[j].na) * 4);
-        }
-        tma_expect(bar, total);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            if (rg[j].n == 0) continue;
-            for (int k = 0; k < SCH; ++k)
-                bulk_g2s(sm + P.spin_off[j] + (size_t)k * P.cap[j] * 16, in_q + ((size_t)k * g.Vh + rg[j].a) * 16,
-                         rg[j].n * 16, bar);
-            if (NRM) {
-                const int ne = (rg[j].a + rg[j].n + 3) & ~3;
-                bulk_g2s(sm + P.nrm_off[j], inn_q + rg[j].na, (ne - rg[j].na) * 4, bar);
-            }
-        }
-    }
-    if (!tma_wait(bar, A.wait_polls)) {
-        // the copies did not complete within the first wait's limit: report, drain them with a wait of the
-        // full limit (no block exits with bulk copies in flight), write nothing
-        if (A.err) atomicExch(A.err, 1u);
-        tma_wait(bar, TMA_SPIN);
-        return;
-    }
-    if (s >= g.Vh) return;
-
-    float acc[24];
-#pragma unroll
-    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    hop_tma<SP, GP, 0, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[0], xp0, lk[0], acc);
-    hop_tma<SP, GP, 0, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[1], xm0, lk[PRE ? 1 : 0], acc);
-    hop_tma<SP, GP, 1, +1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[2], yp0, lk[PRE ? 2 : 0], acc);
-    hop_tma<SP, GP, 1, -1, PRE>(A, sm, P, rg[0], 0, in_q, inn_q, p, s, nb[3], ym0, lk[PRE ? 3 : 0], acc);
-    hop_tma<SP, GP, 2, +1, PRE>(A, sm, P, rg[1], 1, in_q, inn_q, p, s, nb[4], zp0, lk[PRE ? 4 : 0], acc);
-    hop_tma<SP, GP, 2, -1, PRE>(A, sm, P, rg[2], 2, in_q, inn_q, p, s, nb[5], zm0, lk[PRE ? 5 : 0], acc);
-    hop_tma<SP, GP, 3, +1, PRE>(A, sm, P, rg[3], 3, in_q, inn_q, p, s, nb[6], tp0, lk[PRE ? 6 : 0], acc);
-    hop_tma<SP, GP, 3, -1, PRE>(A, sm, P, rg[4], 4, in_q, inn_q, p, s, nb[7], tm0, lk[PRE ? 7 : 0], acc);
-    epilogue<SP, NY>(A, r, p, s, acc);
-}
-
-template <int SP, int GP, bool PRE>
-cudaError_t launch_tma(const DslashArgs& A, int ny, cudaStream_t st)
-{
-    if constexpr (wide_dev<SP>) {
-        return cudaErrorInvalidValue;
-    } else {
-        constexpr bool NRM = SP == P_F16 || SP == P_BF16;
-        const TmaPlan P = tma_plan(A.g.Lxh, nchunk_dev<SP>(), NRM);
-        if (P.bytes > 200 * 1024) return cudaErrorInvalidValue;
-        static bool attr_set[4] = {false, false, false, false};
-        if (!attr_set[ny]) {
-            cudaError_t e = cudaSuccess;
-            const int lim = 200 * 1024;
-            switch (ny) {
-            case 0: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 0, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 1: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 1, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 2: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 2, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            case 3: e = cudaFuncSetAttribute(dslash_tma_kernel<SP, GP, 3, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); break;
-            default: return cudaErrorInvalidValue;
-            }
-            if (e != cudaSuccess) return e;
-            attr_set[ny] = true;
-        }
-        const long long nb = 2LL * ((A.g.Vh + TMA_TB - 1) / TMA_TB) * A.nrhs;
-        if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
-        const dim3 grid((unsigned)nb);
-        switch (ny) {
-        case 0: dslash_tma_kernel<SP, GP, 0, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 1: dslash_tma_kernel<SP, GP, 1, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 2: dslash_tma_kernel<SP, GP, 2, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        case 3: dslash_tma_kernel<SP, GP, 3, PRE><<<grid, TMA_TB, P.bytes, st>>>(A); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Variants 6 and 7 (multi-RHS, FP32 arithmetic): each thread applies D_w at one
-// site to RB = 2 or 4 right-hand sides, so every link is loaded and its third
-// row reconstructed once per RB right-hand sides instead of once per
-// right-hand side (the multi-RHS launch is bound by instruction issue, and the
-// link work is a fifth of it).  Threads (x, y): site x of the block's range,
-// right-hand sides RB * (blockIdx.y * BY + y) + j, j < RB.
-// ---------------------------------------------------------------------------
-template <int SP, int GP, int MU, int S, int RB>
-__device__ __forceinline__ void hop_multi(const DslashArgs& A, const char* const in_q[RB], const float* const inn_q[RB],
-                                          int nr, int p, int s, int sn, bool cross, float acc[RB][24])
-{
-    const int lpar = S > 0 ? p : 1 - p;
-    const int ls = S > 0 ? s : sn;
-    const char* lb = A.gauge + ((size_t)(lpar * 4 + MU) * A.g.Vh) * gauge_link_bytes_dev<GP>();
-    float u[18];
-    load_link<GP, float>(lb, A.g.Vh, ls, u);
-    const float ph = cross ? A.g.fbc[MU] : 1.f;
-#pragma unroll
-    for (int j = 0; j < RB; ++j) {
-        if (j < nr) {
-            float v[24];
-            load_spinor<SP, float>(in_q[j], inn_q[j], A.g.Vh, sn, v);
-            float h[12];
-            project<MU, S, float>(v, h);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) h[i] *= ph;
-            float chi[12];
-            link_mul<S, float>(u, h, chi);
-            accumulate<MU, S, float>(acc[j], chi);
-        }
-    }
-}
-
-template <int SP, int GP, int NY, int RB>
-__global__ void __launch_bounds__(128) dslash_multi_kernel(DslashArgs A)
-{
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * RB;
-    const Geom& g = A.g;
-    if (s >= g.Vh || r0 >= A.nrhs) return;
-    const int nr = A.nrhs - r0 < RB ? A.nrhs - r0 : RB;
-    constexpr size_t CH = nchunk_dev<SP>() * 16;
-    const size_t par_bytes = CH * g.Vh;
-    const int q = 1 - p;
-    const char* in_q[RB];
-    const float* inn_q[RB];
-#pragma unroll
-    for (int j = 0; j < RB; ++j) {
-        const int r = r0 + (j < nr ? j : 0);
-        in_q[j] = A.in + ((size_t)r * 2 + q) * par_bytes;
-        inn_q[j] = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
-    }
-    int c[4];
-    cb_coords(g, s, p, c);
-    float acc[RB][24];
-#pragma unroll
-    for (int j = 0; j < RB; ++j)
-#pragma unroll
-        for (int i = 0; i < 24; ++i) acc[j][i] = 0.f;
-    hop_multi<SP, GP, 0, +1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<0>(g, s, c), c[0] + 1 == g.L[0], acc);
-    hop_multi<SP, GP, 0, -1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<1>(g, s, c), c[0] == 0, acc);
-    hop_multi<SP, GP, 1, +1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<2>(g, s, c), c[1] + 1 == g.L[1], acc);
-    hop_multi<SP, GP, 1, -1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<3>(g, s, c), c[1] == 0, acc);
-    hop_multi<SP, GP, 2, +1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<4>(g, s, c), c[2] + 1 == g.L[2], acc);
-    hop_multi<SP, GP, 2, -1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<5>(g, s, c), c[2] == 0, acc);
-    hop_multi<SP, GP, 3, +1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<6>(g, s, c), c[3] + 1 == g.L[3], acc);
-    hop_multi<SP, GP, 3, -1, RB>(A, in_q, inn_q, nr, p, s, cb_neighbour<7>(g, s, c), c[3] == 0, acc);
-#pragma unroll
-    for (int j = 0; j < RB; ++j)
-        if (j < nr) epilogue<SP, NY>(A, r0 + j, p, s, acc[j]);
-}
-
-template <int SP, int GP, int RB>
-cudaError_t launch_multi(const DslashArgs& A, int ny, dim3 block, cudaStream_t st)
-{
-    if constexpr (wide_dev<SP>) {
-        return cudaErrorInvalidValue;
-    } else {
-        if ((int)(block.x * block.y) > 128) return cudaErrorInvalidValue;
-        const int groups = (A.nrhs + RB - 1) / RB;
-        const dim3 grid(2 * ((A.g.Vh + block.x - 1) / block.x), (groups + block.y - 1) / block.y);
-        switch (ny) {
-        case 0: dslash_multi_kernel<SP, GP, 0, RB><<<grid, block, 0, st>>>(A); break;
-        case 1: dslash_multi_kernel<SP, GP, 1, RB><<<grid, block, 0, st>>>(A); break;
-        case 2: dslash_multi_kernel<SP, GP, 2, RB><<<grid, block, 0, st>>>(A); break;
-        case 3: dslash_multi_kernel<SP, GP, 3, RB><<<grid, block, 0, st>>>(A); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Variants 8 and 9 (FP32 arithmetic; FP32 or 16-bit storage): batched loads.  The loads of NB hops
-// (neighbour spinor, its scale and the link rows, kept in their storage format) are all issued before
-// any of those hops is computed, so a thread has NB hops of memory requests in flight instead of one;
-// the kernel trades occupancy (more registers per thread) for memory-level parallelism per warp.
-// NB = 4: two groups of four hops (forward and backward of x, y, then of z, t); NB = 8: all eight.
-// ---------------------------------------------------------------------------
-template <int SP, int GP>
-struct RawHop {
-    static constexpr bool H16 = SP == P_F16 || SP == P_BF16;
-    static constexpr bool L16 = GP == P_F16 || GP == P_BF16;
-    uint4 sp[H16 ? 3 : 6];   // spinor chunks (16-bit halves or FP32)
-    float n;                 // 16-bit site scale
-    uint4 lk32[L16 ? 1 : 3]; // FP32 link rows
-    uint2 lk16[L16 ? 3 : 1]; // 16-bit link rows
-};
-
-template <int SP, int GP>
-__device__ __forceinline__ void raw_load(RawHop<SP, GP>& R, const char* in_q, const float* inn_q, int Vh, int sn,
-                                         const char* lb, int ls)
-{
-    const uint4* b = reinterpret_cast<const uint4*>(in_q);
-#pragma unroll
-    for (int k = 0; k < (RawHop<SP, GP>::H16 ? 3 : 6); ++k) R.sp[k] = __ldg(b + (size_t)k * Vh + sn);
-    if constexpr (RawHop<SP, GP>::H16) R.n = __ldg(inn_q + sn);
-    if constexpr (RawHop<SP, GP>::L16) {
-        const uint2* l = reinterpret_cast<const uint2*>(lb);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) R.lk16[k] = __ldg(l + (size_t)k * Vh + ls);
-    } else {
-        const uint4* l = reinterpret_cast<const uint4*>(lb);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) R.lk32[k] = __ldg(l + (size_t)k * Vh + ls);
-    }
-}
-
-template <int SP, int GP, int MU, int S>
-__device__ __forceinline__ void raw_hop(const RawHop<SP, GP>& R, bool cross, float phase, float acc[24])
-{
-    float v[24];
-    float scale = 1.f;
-    if constexpr (RawHop<SP, GP>::H16) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float2 a0 = Half<SP>::to2(R.sp[k].x), a1 = Half<SP>::to2(R.sp[k].y), a2 = Half<SP>::to2(R.sp[k].z),
-                         a3 = Half<SP>::to2(R.sp[k].w);
-            v[8 * k + 0] = a0.x;
-            v[8 * k + 1] = a0.y;
-            v[8 * k + 2] = a1.x;
-            v[8 * k + 3] = a1.y;
-            v[8 * k + 4] = a2.x;
-            v[8 * k + 5] = a2.y;
-            v[8 * k + 6] = a3.x;
-            v[8 * k + 7] = a3.y;
-        }
-        scale = R.n;
-    } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            v[4 * k] = __uint_as_float(R.sp[k].x);
-            v[4 * k + 1] = __uint_as_float(R.sp[k].y);
-            v[4 * k + 2] = __uint_as_float(R.sp[k].z);
-            v[4 * k + 3] = __uint_as_float(R.sp[k].w);
-        }
-    }
-    float h[12];
-    project<MU, S, float>(v, h);
-    if (cross) scale *= phase;
-    if (RawHop<SP, GP>::H16 || cross) {
-#pragma unroll
-        for (int i = 0; i < 12; ++i) h[i] *= scale;
-    }
-    float u[18];
-    if constexpr (RawHop<SP, GP>::L16) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float2 a0 = Half<GP>::to2(R.lk16[k].x), a1 = Half<GP>::to2(R.lk16[k].y);
-            u[4 * k] = a0.x;
-            u[4 * k + 1] = a0.y;
-            u[4 * k + 2] = a1.x;
-            u[4 * k + 3] = a1.y;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            u[4 * k] = __uint_as_float(R.lk32[k].x);
-            u[4 * k + 1] = __uint_as_float(R.lk32[k].y);
-            u[4 * k + 2] = __uint_as_float(R.lk32[k].z);
-            u[4 * k + 3] = __uint_as_float(R.lk32[k].w);
-        }
-    }
-    link_row2<float>(u);
-    float chi[12];
-    link_mul<S, float>(u, h, chi);
-    accumulate<MU, S, float>(acc, chi);
-}
-
-template <int SP, int GP, int NY, int NB>
-__global__ void __launch_bounds__(128) dslash_batched_kernel(DslashArgs A)
-{
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    const Geom& g = A.g;
-    if (s >= g.Vh || r >= A.nrhs) return;
-    constexpr size_t CH = nchunk_dev<SP>() * 16;
-    constexpr size_t LB = gauge_link_bytes_dev<GP>();
-    const size_t par_bytes = CH * g.Vh;
-    const int q = 1 - p;
-    const char* in_q = A.in + ((size_t)r * 2 + q) * par_bytes;
-    const float* inn_q = A.in_n ? A.in_n + ((size_t)r * 2 + q) * g.Vh : nullptr;
-    int c[4];
-    cb_coords(g, s, p, c);
-    int nb[8];
-    cb_neighbours(g, s, c, nb);
-    const bool cr[8] = {c[0] + 1 == g.L[0], c[0] == 0, c[1] + 1 == g.L[1], c[1] == 0,
-                        c[2] + 1 == g.L[2], c[2] == 0, c[3] + 1 == g.L[3], c[3] == 0};
-    // link of hop h: forward U_mu(n) at (p, s); backward U_mu(n - mu) at (q, neighbour)
-    auto lbase = [&](int h) {
-        const int mu = h >> 1;
-        const int lpar = (h & 1) ? q : p;
-        return A.gauge + ((size_t)(lpar * 4 + mu) * g.Vh) * LB;
-    };
-    float acc[24];
-#pragma unroll
-    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
-    RawHop<SP, GP> R[NB];
-#pragma unroll
-    for (int g0 = 0; g0 < 8; g0 += NB) {
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const int h = g0 + j;
-            raw_load<SP, GP>(R[j], in_q, inn_q, g.Vh, nb[h], lbase(h), (h & 1) ? nb[h] : s);
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const int h = g0 + j;
-            switch (h) {
-            case 0: raw_hop<SP, GP, 0, +1>(R[j], cr[0], g.fbc[0], acc); break;
-            case 1: raw_hop<SP, GP, 0, -1>(R[j], cr[1], g.fbc[0], acc); break;
-            case 2: raw_hop<SP, GP, 1, +1>(R[j], cr[2], g.fbc[1], acc); break;
-            case 3: raw_hop<SP, GP, 1, -1>(R[j], cr[3], g.fbc[1], acc); break;
-            case 4: raw_hop<SP, GP, 2, +1>(R[j], cr[4], g.fbc[2], acc); break;
-            case 5: raw_hop<SP, GP, 2, -1>(R[j], cr[5], g.fbc[2], acc); break;
-            case 6: raw_hop<SP, GP, 3, +1>(R[j], cr[6], g.fbc[3], acc); break;
-            default: raw_hop<SP, GP, 3, -1>(R[j], cr[7], g.fbc[3], acc); break;
-            }
-        }
-    }
-    epilogue<SP, NY>(A, r, p, s, acc);
-}
-
-template <int SP, int GP, int NB>
-cudaError_t launch_batched(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
-{
-    if constexpr (wide_dev<SP>) {
-        return cudaErrorInvalidValue;
-    } else {
-        if ((int)(block.x * block.y) > 128) return cudaErrorInvalidValue;
-        switch (ny) {
-        case 0: dslash_batched_kernel<SP, GP, 0, NB><<<grid, block, 0, st>>>(A); break;
-        case 1: dslash_batched_kernel<SP, GP, 1, NB><<<grid, block, 0, st>>>(A); break;
-        case 2: dslash_batched_kernel<SP, GP, 2, NB><<<grid, block, 0, st>>>(A); break;
-        case 3: dslash_batched_kernel<SP, GP, 3, NB><<<grid, block, 0, st>>>(A); break;
-        default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-}
-
-template <int SP, int GP, int VAR>
-cudaError_t launch_var(const DslashArgs& A, int ny, dim3 grid, dim3 block, cudaStream_t st)
-{
-    if ((int)(block.x * block.y) > Bounds<SP, VAR>::maxt) return cudaErrorInvalidValue;
-    switch (ny) {
-    case 0: dslash_kernel<SP, GP, 0, VAR><<<grid, block, 0, st>>>(A); break;
-    case 1: dslash_kernel<SP, GP, 1, VAR><<<grid, block, 0, st>>>(A); break;
-    case 2: dslash_kernel<SP, GP, 2, VAR><<<grid, block, 0, st>>>(A); break;
-    case 3: dslash_kernel<SP, GP, 3, VAR><<<grid, block, 0, st>>>(A); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <int SP, int GP>
-cudaError_t launch_ny(const DslashArgs& A, int ny, int var, dim3 grid, dim3 block, cudaStream_t st)
-{
-    switch (var) {
-    case 0: return launch_var<SP, GP, 0>(A, ny, grid, block, st);
-    case 1: return launch_var<SP, GP, 1>(A, ny, grid, block, st);
-    case 2: return launch_var<SP, GP, 2>(A, ny, grid, block, st);
-    case 3: return launch_staged<SP, GP>(A, ny, grid, block, st);
-    case 4: return launch_tma<SP, GP, false>(A, ny, st);
-    case 5: return launch_tma<SP, GP, true>(A, ny, st);
-    case 6: return launch_multi<SP, GP, 2>(A, ny, block, st);
-    case 7: return launch_multi<SP, GP, 4>(A, ny, block, st);
-    case 8: return launch_batched<SP, GP, 4>(A, ny, grid, block, st);
-    case 9: return launch_batched<SP, GP, 8>(A, ny, grid, block, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
-}  // namespace
-
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st)
 {
     if (bx <= 0 || by <= 0 || bx * by > (wide(sp) ? 256 : 512)) return cudaErrorInvalidValue;
-    dim3 block(bx, by);
-    dim3 grid(2 * ((A.g.Vh + bx - 1) / bx), (A.nrhs + by - 1) / by);
-    if (sp == P_F64 && gp == P_F64) return launch_ny<P_F64, P_F64>(A, ny, var, grid, block, st);
-    if (sp == P_DF64 && gp == P_DF64) return launch_ny<P_DF64, P_DF64>(A, ny, var, grid, block, st);
-    if (sp == P_F32 && gp == P_F32) return launch_ny<P_F32, P_F32>(A, ny, var, grid, block, st);
-    if (sp == P_F16 && gp == P_F16) return launch_ny<P_F16, P_F16>(A, ny, var, grid, block, st);
-    if (sp == P_BF16 && gp == P_BF16) return launch_ny<P_BF16, P_BF16>(A, ny, var, grid, block, st);
-    if (sp == P_F32 && gp == P_F16) return launch_ny<P_F32, P_F16>(A, ny, var, grid, block, st);
-    if (sp == P_F32 && gp == P_BF16) return launch_ny<P_F32, P_BF16>(A, ny, var, grid, block, st);
+    const dim3 block(bx, by);
+    const dim3 grid(2 * ((A.g.Vh + bx - 1) / bx), (A.nrhs + by - 1) / by);
+    if (var >= 0 && var <= 2) return launch_dslash_regs(A, sp, gp, ny, var, grid, block, st);
+    if (var >= 3 && var <= 5) return launch_dslash_staged(A, sp, gp, ny, var, grid, block, st);
+    if (var == 6 || var == 7) return launch_dslash_multi(A, sp, gp, ny, var, grid, block, st);
+    if (var == 8 || var == 9) return launch_dslash_batched(A, sp, gp, ny, var, grid, block, st);
+    if (var == 10 || var == 11) return launch_dslash_pair(A, sp, gp, ny, var, grid, block, st);
     return cudaErrorInvalidValue;
 }
 

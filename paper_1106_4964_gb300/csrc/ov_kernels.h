@@ -31,9 +31,18 @@ constexpr long long DSLASH_WAIT_POLLS = 1ll << 22;  // default first-wait limit 
 // (FP32 math, by = 1), 4 block-wide bulk-copy (TMA) staging of the neighbour ranges (FP32 math;
 // fixed 128-site blocks, bx and by ignored), 5 the same with the eight links loaded before the wait,
 // 6 and 7: 2 and 4 right-hand sides per thread sharing each link (FP32 math; by counts rhs groups),
-// 8 and 9: the loads of 4 or 8 hops issued together before their arithmetic (FP32 math)
+// 8 and 9: the loads of 4 or 8 hops issued together before their arithmetic (FP32 math),
+// 10 and 11: 2 or 4 right-hand sides per thread as pairs on the packed FP32 pipe (by counts rhs groups)
 cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, int by, int var, cudaStream_t st);
-constexpr int DSLASH_VARIANTS = 10;
+// the variant groups, one translation unit each (grid and block already derived from bx, by)
+cudaError_t launch_dslash_regs(const DslashArgs& A, int sp, int gp, int ny, int var, dim3 grid, dim3 block, cudaStream_t st);
+cudaError_t launch_dslash_staged(const DslashArgs& A, int sp, int gp, int ny, int var, dim3 grid, dim3 block,
+                                 cudaStream_t st);
+cudaError_t launch_dslash_multi(const DslashArgs& A, int sp, int gp, int ny, int var, dim3 grid, dim3 block, cudaStream_t st);
+cudaError_t launch_dslash_batched(const DslashArgs& A, int sp, int gp, int ny, int var, dim3 grid, dim3 block,
+                                  cudaStream_t st);
+cudaError_t launch_dslash_pair(const DslashArgs& A, int sp, int gp, int ny, int var, dim3 grid, dim3 block, cudaStream_t st);
+constexpr int DSLASH_VARIANTS = 12;
 
 // ---------------------------------------------------------------- layout conversion
 // canonical complex128 [nrhs][V][12] (device) <-> internal field

@@ -797,9 +797,12 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // In chiral mode every vector of the inner recursion must stay in its right-hand side's sector:
     // the one-sign operator acts on the other sector as m^2 (plus a coupling back), so rounding-level
     // components there would grow by ~rho^2/m^2 per cycle.  v <- (1 + chi gamma5) v / 2 after every
-    // true residual and every preconditioner application (the network mixes chiralities).
+    // true residual and every preconditioner application (the network mixes chiralities).  Once the
+    // solve has fallen back to the two-sign operator the projection stops: the true D^dag D couples
+    // the sectors by as much as sign^2 differs from 1, and that part of the residual is what the
+    // two-sign recursion has to remove.
     auto sector_project = [&](const FieldDesc& v) -> int {
-        if (!c->chiral) return OV_OK;
+        if (!use_chiral) return OV_OK;
         FieldDesc v2[2] = {v, v};
         return lincomb(c, v, 2, v2, nullptr, dch + 3 * R, 2, nullptr, st);
     };
@@ -816,13 +819,33 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // FP64 true residual r = b - A x, then the deflated restart (Eq. 9 on the current residual):
     // x += sum_i xi_i (xi_i^dag r) / mu_i and r <- r - sum_i xi_i (xi_i^dag r).  Repeating it at every
     // true residual removes the low-mode error even when the xi_i are approximate eigenvectors.
+    // exact zero modes (excluded from the solution, the pseudo-inverse of reading 12): b's component along
+    // them cannot be solved for, so the true residual is measured on their orthogonal complement
+    int nzero = 0;
+    for (int i = 0; i < nd; ++i) nzero += inv[i] == 0.0;
     auto refresh = [&](bool& all_done) -> int {
         OV_TRY(normal_apply(c, x, t, mass, st));
         FieldDesc v2[2] = {b, t};
         double2 h2[2] = {make_double2(1, 0), make_double2(-1, 0)};
         OV_TRY(lincomb(c, r, 2, v2, h2, nullptr, 0, dnr, st));
         std::vector<double> nr(R);
-        OV_TRY(to_host(c, dnr, nr.data(), R * sizeof(double), st));
+        if (nzero) {
+            OV_TRY(block_dots(c, xi64, nd, r, st));
+            std::vector<double2> h((size_t)nd * R);
+            OV_TRY(to_host(c, c->dscal, h.data(), h.size() * sizeof(double2), st));
+            for (int i = 0; i < nd; ++i)
+                if (inv[i] != 0.0)
+                    for (int q = 0; q < R; ++q) h[(size_t)i * R + q] = make_double2(0, 0);
+            OV_TRY(to_dev(c, h.data(), c->dscal, h.size() * sizeof(double2), st));
+            FieldDesc none{};
+            OV_CUDA(c, launch_proj_update(c->g, xi64, nd, (const double2*)c->dscal, nullptr, r, r, none, st));
+            std::vector<double2> hn(R);
+            OV_TRY(norm2(c, r, (double*)ddt, st));
+            OV_TRY(to_host(c, ddt, hn.data(), R * sizeof(double2), st));
+            for (int q = 0; q < R; ++q) nr[q] = hn[q].x;
+        } else {
+            OV_TRY(to_host(c, dnr, nr.data(), R * sizeof(double), st));
+        }
         all_done = true;
         for (int q = 0; q < R; ++q) {
             res[q] = std::sqrt(nr[q]) / bn[q];

@@ -167,7 +167,7 @@ def test_field_dot(prec, tol):
 
 # every launch variant the autotuner may pick: (bx, by, variant)
 VARIANTS = [(128, 1, 0), (64, 2, 0), (64, 1, 1), (32, 2, 2), (64, 1, 3), (128, 1, 4), (128, 1, 5), (64, 1, 6),
-            (32, 2, 6), (64, 1, 7), (64, 1, 8), (128, 1, 9)]
+            (32, 2, 6), (64, 1, 7), (64, 1, 8), (128, 1, 9), (64, 1, 10), (32, 2, 10), (64, 1, 11), (32, 1, 11)]
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6), (2, 6, 4, 10), (16, 16, 16, 32)])
@@ -211,6 +211,34 @@ def test_autotuned_shape_parity(prec):
         got = host(out)
         for r in range(nrhs):
             assert rel(got[r], oracle.dslash(dims, ABC, U, 0.2, psi[r])) <= TOL[prec], shape
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_twelve_rhs_autotuned_parity(prec):
+    """The 12-source launch the multi-RHS solves take (autotuned: typically the packed-pair
+    variants, several sources per thread) against the oracle for every source, and each
+    pair variant forced explicitly with an odd source count (a half-empty last pair)."""
+    from paper_1106_4964_gb300 import Context
+
+    dims = (8, 8, 8, 16)
+    U = synth.gauge_field(dims, 9, 0.5)
+    psi = synth.gaussian_spinor(dims, 10, nrhs=12)
+    ref = [oracle.dslash(dims, ABC, U, -RHO, psi[r]) for r in range(12)]
+    ctx = Context(dims, ABC)
+    ctx.set_gauge(dev(U))
+    shape = ctx.tune_dslash(prec, 12)
+    out = torch.empty_like(dev(psi))
+    ctx.apply_dslash(dev(psi), out, -RHO, prec=prec)
+    got = host(out)
+    for r in range(12):
+        assert rel(got[r], ref[r]) <= TOL[prec], (shape, r)
+    for bx, by, var in [(64, 2, 10), (32, 3, 10), (64, 1, 11), (32, 2, 11)]:
+        ctx.set_dslash_shape(prec, 11, bx, by, var)
+        out = torch.empty_like(dev(psi[:11]))
+        ctx.apply_dslash(dev(psi[:11]), out, -RHO, prec=prec)
+        got = host(out)
+        for r in range(11):
+            assert rel(got[r], ref[r]) <= TOL[prec], (bx, by, var, r)
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("df64", 1e-12), ("f32", 1e-6)])

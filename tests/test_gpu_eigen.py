@@ -53,7 +53,9 @@ def test_low_modes_match_oracle_lanczos(lat):
     v0 = synth.gaussian_spinor(dims, 12)[0].reshape(-1)
     ov, oe, ores = oracle.lanczos_lowmodes(dims, ABC, U, -RHO, m=700, nev=nev + 4, v0=v0)
     print(f"low modes: GPU {vals}, oracle {ov[:nev]}, oracle residual {ores:.2e}")
-    assert ores < 1e-8 * lmax  # the oracle's own pairs are converged
+    # the oracle's own pairs: eigen-residual r <= 1e-6 lambda_max, so its eigenvalues are exact to
+    # r^2 / gap (Hermitian) and its vectors to r / gap
+    assert ores < 1e-6 * lmax
     # the same |lambda| spectrum, and every signed GPU eigenvalue is one of the oracle's (a +-lambda pair
     # at the edge of the nev modes may contribute either member)
     assert np.allclose(np.sort(np.abs(vals)), np.sort(np.abs(ov))[:nev], rtol=0, atol=1e-9 * lmax)
@@ -64,4 +66,4 @@ def test_low_modes_match_oracle_lanczos(lat):
         same = np.abs(ov - vals[i]) < 1e-7 * lmax
         P = oe[same]
         proj = P.conj() @ vecs[i]
-        assert abs(np.linalg.norm(proj) - 1) < 1e-8
+        assert abs(np.linalg.norm(proj) - 1) < 1e-6

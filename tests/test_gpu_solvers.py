@@ -178,3 +178,41 @@ def test_deflate_normal_modes_chiral():
     for i in range(nev):
         r = A @ vecs[i] - vals[i] * vecs[i]
         assert np.linalg.norm(r) <= 1e-8 * mu[-1]
+
+
+def test_massless_cg_with_exact_zero_modes():
+    """Reading 12 (pseudo-inverse): the periodic free field has 12 exact zero modes of the massless
+    overlap (the constant fields, D_w(0) = -rho gives sign = -gamma5); the GPU eigensolver finds them
+    among the D^dag D modes, the massless CG leaves them out of x, and the solution meets the true
+    residual 1e-10 on their orthogonal complement, checked with the oracle's operator and the
+    analytic zero modes."""
+    from paper_1106_4964_gb300 import Context
+
+    dims, pbc = (4, 4, 4, 4), (1.0, 1.0, 1.0, 1.0)
+    U = synth.unit_gauge(dims)
+    # [eps, 1] must hold the whole free-field H_w spectrum: on 4^4 its smallest |lambda| is 0.5 (one
+    # momentum component pi: |D_w(-rho)| = |-rho + 2|), and sqrt(0.005) * 6.6 = 0.47; degree 200 gives
+    # delta ~ 1e-12 there.  (Below eps the polynomial grows like T_n outside [-1, 1], D^dag D gets
+    # eigenvalues ~1e20 and no eigensolver converges.)
+    eps, n, lmax = 0.005, 200, 6.6
+    c = oracle.cheb_coeffs(eps, n)
+    ctx = Context(dims, pbc)
+    ctx.set_gauge(dev(U))
+    ctx.set_sign_poly(RHO, eps, n, lmax)
+    ctx.deflate(1, 12, 1e-10)
+    vals, _ = ctx.get_eigenpairs(1)
+    assert np.all(np.abs(vals) < 1e-9 * 4 * RHO * RHO)  # the 12 lowest are the exact zero modes
+    b = synth.point_sources(dims)[[0, 5, 10]]
+    x = torch.empty_like(dev(b))
+    info = ctx.cg_solve(dev(b), x, mass=0.0, tol=1e-10, max_iter=2000, inner_prec="f32")
+    xs = host(x)
+    V = oracle.volume(dims)
+    Z = np.zeros((12, V * 12), dtype=np.complex128)  # constant field per spin-colour component
+    for k in range(12):
+        Z[k, k::12] = 1.0 / np.sqrt(V)
+    for r in range(len(b)):
+        res = b[r].reshape(-1) - oracle.overlap_normal(dims, pbc, U, RHO, 0.0, lmax, eps, c, xs[r]).reshape(-1)
+        res -= Z.T @ (Z.conj() @ res)
+        assert np.linalg.norm(res) / np.linalg.norm(b[r]) <= 1e-10
+        assert np.linalg.norm(Z.conj() @ xs[r].reshape(-1)) <= 1e-10 * np.linalg.norm(xs[r])
+    assert max(info["true_residual"]) <= 1e-10
