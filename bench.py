@@ -107,6 +107,18 @@ def site_bytes(prec: str, nrhs: int = 1) -> float:
     return 48 * rb / nrhs + 2 * spin
 
 
+def clenshaw_step_bytes(prec: str, nrhs: int, f32_work: bool) -> float:
+    """Compulsory bytes per site and RHS of one Clenshaw step (two D_w launches, the second with the
+    fused epilogue b_k = c_k psi_h + alpha H_w t + beta b_{k+1} - b_{k+2}): twice the D_w bytes plus the
+    three epilogue fields.  16-bit storage with FP32 recurrence fields (the library's default) moves
+    FP32 spinors and 16-bit links."""
+    work = "f32" if (prec in ("f16", "bf16") and f32_work) else prec
+    rb = REAL_BYTES[work]
+    spin = 24 * rb + (4 if work in ("f16", "bf16") else 0)
+    links = 48 * REAL_BYTES[prec] / nrhs
+    return 2 * (links + 2 * spin) + 3 * spin
+
+
 class Clocks:
     """Samples nvidia-smi every 200 ms in the background."""
 
@@ -555,6 +567,7 @@ def run_overlap(args):
     import synth
 
     U = synth.gauge_field(dims, seed=1, s=0.5, ape_steps=3)
+    hbm, _ = peaks()
     ctx = ov.Context(dims, BC)
     ctx.set_gauge(torch.from_numpy(U).cuda())
     t0 = time.perf_counter()
@@ -598,8 +611,13 @@ def run_overlap(args):
             err = None
             if nrhs == 1 and ref is not None:
                 err = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+            steps = launches / 2.0  # Clenshaw steps (the final D_w launch counted as half a step)
+            cb = clenshaw_step_bytes(prec, nrhs, bool(ctx.get_option("clenshaw_f32")))
+            gbs = steps * V * nrhs * cb / (ms * 1e-3) / 1e9
             res[f"{prec}_r{nrhs}"] = {"ms": round(ms, 3), "applications_per_s": round(1e3 * nrhs / ms, 3),
-                                      "dslash_launches": int(launches), "rel_err_vs_f64": err}
+                                      "dslash_launches": int(launches), "rel_err_vs_f64": err,
+                                      "us_per_launch": round(1e3 * ms / max(1, launches), 2),
+                                      "clenshaw_step_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
             fi.close()
             fo.close()
     main = res["f32_r1"]
@@ -823,7 +841,11 @@ def run_learned(args):
     t0 = time.perf_counter()
     cs = prepare(small)
     loss = cs.net_train(nsolves=args.train_solves, steps=args.train_steps, lr=args.lr, mass=args.mass)
-    res["train"] = {"seconds": round(time.perf_counter() - t0, 1), "pairs": cs.net_pairs(), "loss_per_pair": loss}
+    curve = cs.net_loss_history()
+    res["train"] = {"seconds": round(time.perf_counter() - t0, 1), "pairs": cs.net_pairs(), "loss_per_pair": loss,
+                    "loss_curve": {str(i): round(float(curve[i]), 5)
+                                   for i in sorted(set(list(range(0, len(curve), max(1, len(curve) // 20)))
+                                                       + [len(curve) - 1]))}}
     w = cs.net_weights()
     cs.close()
     cb = prepare(big)

@@ -217,6 +217,11 @@ int ov_net_loss_grad(ov_ctx* ctx, const void* r, const void* e, int npairs, doub
                      void* stream);
 /* Number of training pairs recorded by the last ov_net_train. */
 int ov_net_pairs(const ov_ctx* ctx);
+/* Loss curve of the last ov_net_train: the mean loss per pair before each
+ * Adam step and after the last one (steps + 1 values).  Copies up to cap of
+ * them to out and returns how many there are (0 before any training;
+ * -OV_EINVAL for a bad argument). */
+int ov_net_loss_history(const ov_ctx* ctx, double* out, int cap);
 
 /* ---- internal-layout fields: an even/odd field kept on the device in one
  * storage precision, for chaining operators without repacking. ---- */

@@ -68,6 +68,7 @@ _SIGS = {
     "ov_net_apply": (_I, [_P, _P, _P, _I, _P]),
     "ov_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(_D), _P, _P]),
     "ov_net_pairs": (_I, [_P]),
+    "ov_net_loss_history": (_I, [_P, _P, _I]),
     "ov_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
     "ov_field_destroy": (_I, [_P]),
     "ov_field_import": (_I, [_P, _P, _P, _P]),
@@ -346,6 +347,16 @@ class Context:
 
     def net_pairs(self):
         return int(self.lib.ov_net_pairs(self.h))
+
+    def net_loss_history(self):
+        """Mean loss per pair before each Adam step of the last net_train, and after the last."""
+        n = int(self.lib.ov_net_loss_history(self.h, None, 0))
+        if n < 0:
+            raise OverlapError(-n, "ov_net_loss_history")
+        out = np.empty(n)
+        if n:
+            self.lib.ov_net_loss_history(self.h, _ptr(out), n)
+        return out
 
     def field(self, nrhs, prec):
         return Field(self, nrhs, prec)

@@ -35,7 +35,7 @@ enum Slot {
     WS_IN = 0, WS_OUT, WS_PH, WS_W, WS_T, WS_B0, WS_B1, WS_B2,
     WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_Q, WS_CG_Z, WS_CG_B, WS_CG_T, WS_CG_U, WS_CG_RS, WS_CG_PS, WS_CG_QS, WS_CG_XS,
     WS_CG_BH, WS_CG_XH, WS_TC0, WS_TC1, WS_MX0, WS_MX1, WS_RS, WS_RR, WS_RP, WS_RQ, WS_RT,
-    WS_LZ_W, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
+    WS_LZ_W, WS_LZ_WB, WS_LZ_T, WS_LZ_F0, WS_LZ_F1, WS_LZ_F2, WS_LZ_F3, WS_NET_S, WS_NET_H, WS_NET_G, WS_NET_GH, WS_AUX0, WS_AUX1,
     WS_COUNT
 };
 

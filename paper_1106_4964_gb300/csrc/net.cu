@@ -43,6 +43,7 @@ struct NetState {
     int recording = 0;
     FieldDesc pr{}, px{};
     int npairs = 0, cap = 0;
+    std::vector<double> history;  // mean loss per pair before each Adam step of the last training
 };
 
 namespace {
@@ -626,8 +627,10 @@ int ov_net_train(ov_ctx* c, int nsolves, int steps, double lr, double mass, doub
     // ---- Adam over all recorded pairs
     double loss = 0;
     const float b1 = 0.9f, b2 = 0.999f;
+    n->history.clear();
     for (int it = 0; it < steps; ++it) {
         OV_TRY(loss_grad(c, n->pr, n->px, 0, n->npairs, &loss, st));
+        n->history.push_back(loss / n->npairs);
         ++n->adam_t;
         const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
         const float lr_t = (float)(lr * (it < steps / 2 ? 1.0 : 0.3));
@@ -638,11 +641,21 @@ int ov_net_train(ov_ctx* c, int nsolves, int steps, double lr, double mass, doub
     }
     OV_TRY(loss_grad(c, n->pr, n->px, 0, n->npairs, &loss, st));  // also refreshes the adjoint weights
     if (final_loss) *final_loss = loss / n->npairs;
+    n->history.push_back(loss / n->npairs);
     n->trained = 1;
     n->adj_valid = 1;
     return OV_OK;
 }
 
 int ov_net_pairs(const ov_ctx* c) { return c && c->net ? c->net->npairs : 0; }
+
+int ov_net_loss_history(const ov_ctx* c, double* out, int cap)
+{
+    if (!c || cap < 0 || (cap > 0 && !out)) return -OV_EINVAL;
+    if (!c->net) return 0;
+    const auto& h = c->net->history;
+    for (int i = 0; i < cap && i < (int)h.size(); ++i) out[i] = h[i];
+    return (int)h.size();
+}
 
 }  // extern "C"

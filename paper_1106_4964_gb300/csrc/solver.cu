@@ -307,7 +307,7 @@ int project_chiral(ov_ctx* c, const FieldDesc& v, int chi, cudaStream_t st)
 }
 
 struct LanczosWork {
-    FieldDesc basis, rot, zero, w, tmp[4];
+    FieldDesc basis, rot, zero, w, wb, tmp[4];  // wb: FP64 batch of the filter (FB right-hand sides)
 };
 
 // Chebyshev-filtered subspace iteration for the nev smallest eigenpairs of the Hermitian A on
@@ -396,6 +396,27 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         OV_TRY(orth_into(j, seed + j));
     }
 
+    // |op(B_{w0+q}) - lam[q] B_{w0+q}| for the FB vectors of B from w0 (one multi-RHS application),
+    // into rwin[q]
+    const int FB = W.wb.nrhs;
+    std::vector<double> rwin(FB);
+    auto residual_window = [&](const OpFn& op, const FieldDesc& B, int w0, const double* lam, int n) -> int {
+        OV_TRY(op(sub(B, w0, n), W.wb));
+        std::vector<double2> co(2 * n);
+        for (int q = 0; q < n; ++q) {
+            co[q] = make_double2(1, 0);
+            co[n + q] = make_double2(-lam[q], 0);
+        }
+        double2* dco = (double2*)(c->dscal + DSCAL_CGCO);
+        double* dnr = c->dscal + DSCAL_NORM;
+        OV_TRY(to_dev(c, co.data(), dco, co.size() * sizeof(double2), st));
+        FieldDesc xs[2] = {W.wb, sub(B, w0, n)};
+        OV_TRY(lincomb(c, W.wb, 2, xs, nullptr, dco, 0, dnr, st));
+        std::vector<double> n2(n);
+        OV_TRY(to_host(c, dnr, n2.data(), n * sizeof(double), st));
+        for (int q = 0; q < n; ++q) rwin[q] = std::sqrt(std::max(0.0, n2[q]));
+        return OV_OK;
+    };
     std::vector<double> theta(nb, 0.0), res(nb, 1e300);
     int nlock = 0;
     double tscale = 1.0;  // tightens the locking threshold when the final R check fails
@@ -412,19 +433,47 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         const double limit = W.tmp[0].prec == P_F64 ? 1e12 : (W.tmp[0].prec == P_DF64 ? 1e10 : 1e4);
         const int kmax = (int)std::floor(std::acosh(limit) / std::acosh(y0));
         const int Keff = std::max(2, std::min(K, kmax)) & ~1;
-        for (int j = nlock; j < nb; ++j) {
-            OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, sub(V, j), W.w, W.tmp, st));
-            OV_TRY(project_chiral(c, W.w, chi, st));
-            OV_TRY(orth_into(j, seed + 31ull * it + j));
+        // The unlocked vectors are filtered FB at a time as one multi-RHS field (the multi-RHS
+        // operator costs less per vector than FB single ones), a window of exactly FB vectors so that
+        // every batch reuses the same work fields (the last window reaches back over vectors already
+        // done, whose filtered copies are dropped).  The batch is orthogonalised against V[0, j0) by
+        // a block CGS2 (one pass over V per pass for all FB vectors), then each vector against the
+        // batch vectors placed before it.
+        for (int j0 = nlock; j0 < nb; j0 += FB) {
+            const int w0 = std::max(0, std::min(j0, nb - FB));
+            OV_TRY(cheb_filter(c, AcW, Keff, acut, bmax, sub(V, w0, FB), W.wb, W.tmp, st));
+            OV_TRY(project_chiral(c, W.wb, chi, st));
+            if (j0 > 0)
+                for (int pass = 0; pass < 2; ++pass) {
+                    OV_TRY(block_dots(c, V, j0, W.wb, st));
+                    OV_TRY(block_sub(c, V, j0, W.wb, st));
+                }
+            for (int j = j0; j < std::min(j0 + FB, nb); ++j) {
+                OV_TRY(copy_field(c, sub(W.wb, j - w0), W.w, st));
+                std::vector<cd> h;
+                if (j > j0) OV_TRY(cgs2(c, sub(V, j0, j - j0), j - j0, W.w, h, st));
+                const double nr = host_norm(c, W.w, st, &status);
+                OV_TRY(status);
+                if (nr > 1e-200)
+                    OV_TRY(scale_into(c, W.w, sub(V, j), 1.0 / nr, st));
+                else
+                    OV_TRY(orth_into(j, seed + 31ull * it + j));  // vanished: a random vector in its place
+            }
         }
-        // Rayleigh-Ritz with A over the block (locked vectors keep their Ritz values)
+        // Rayleigh-Ritz with A over the block (locked vectors keep their Ritz values); the columns
+        // A V_j in windows of FB vectors, like the filter
         std::vector<cd> G((size_t)nb * nb, cd(0, 0));
-        for (int j = nlock; j < nb; ++j) {
-            OV_TRY(Ac(sub(V, j), W.w));
-            OV_TRY(block_dots(c, V, nb, W.w, st));
-            std::vector<double2> hh(nb);
-            OV_TRY(to_host(c, c->dscal, hh.data(), nb * sizeof(double2), st));
-            for (int i = 0; i < nb; ++i) G[(size_t)i * nb + j] = cd(hh[i].x, hh[i].y);
+        for (int j0 = nlock; j0 < nb; j0 += FB) {
+            const int w0 = std::max(0, std::min(j0, nb - FB));
+            OV_TRY(Ac(sub(V, w0, FB), W.wb));
+            OV_TRY(block_dots(c, V, nb, W.wb, st));
+            std::vector<double2> hh((size_t)nb * FB);
+            OV_TRY(to_host(c, c->dscal, hh.data(), hh.size() * sizeof(double2), st));
+            for (int j = j0; j < std::min(j0 + FB, nb); ++j)
+                for (int i = 0; i < nb; ++i) {
+                    const double2 v = hh[(size_t)i * FB + (j - w0)];
+                    G[(size_t)i * nb + j] = cd(v.x, v.y);
+                }
         }
         for (int i = 0; i < nb; ++i) {
             if (i < nlock) {
@@ -449,15 +498,18 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
         // extends, past nev when it can (a few block vectors stay unlocked as a buffer).
         nlock = 0;
         const int jmax = std::max(nev, nb - 4);
-        for (int j = 0; j < jmax; ++j) {
-            OV_TRY(Ac(sub(V, j), W.w));
-            FieldDesc xs[2] = {W.w, sub(V, j)};
-            const double2 h2[2] = {make_double2(1, 0), make_double2(-theta[j], 0)};
-            OV_TRY(lincomb(c, W.w, 2, xs, h2, nullptr, 0, nullptr, st));
-            res[j] = host_norm(c, W.w, st, &status);
-            OV_TRY(status);
-            if (j == nlock && res[j] <= tolA(theta[j])) ++nlock;
-            if (j >= nev - 1 && j >= nlock) break;  // the locked run ended
+        bool ended = false;
+        for (int j0 = 0; j0 < jmax && !ended; j0 += FB) {
+            const int w0 = std::max(0, std::min(j0, nb - FB));
+            OV_TRY(residual_window(Ac, V, w0, theta.data() + w0, FB));
+            for (int j = j0; j < std::min(j0 + FB, jmax); ++j) {
+                res[j] = rwin[j - w0];
+                if (j == nlock && res[j] <= tolA(theta[j])) ++nlock;
+                if (j >= nev - 1 && j >= nlock) {  // the locked run ended
+                    ended = true;
+                    break;
+                }
+            }
         }
         if (verbose())
             fprintf(stderr, "[ov] chfsi chi=%d it %d: cut %.4e, degree %d, locked %d (want %d), res[nev-1] %.3e\n", chi,
@@ -470,12 +522,17 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             // mode below the largest accepted |lambda| is left out of the deflation.
             const int nr = nlock;
             std::vector<cd> M((size_t)nr * nr);
-            for (int j = 0; j < nr; ++j) {
-                OV_TRY(R(sub(V, j), W.w));
-                OV_TRY(block_dots(c, V, nr, W.w, st));
-                std::vector<double2> hh(nr);
-                OV_TRY(to_host(c, c->dscal, hh.data(), nr * sizeof(double2), st));
-                for (int i = 0; i < nr; ++i) M[(size_t)i * nr + j] = cd(hh[i].x, hh[i].y);
+            for (int j0 = 0; j0 < nr; j0 += FB) {
+                const int w0 = std::max(0, std::min(j0, nb - FB));
+                OV_TRY(R(sub(V, w0, FB), W.wb));
+                OV_TRY(block_dots(c, V, nr, W.wb, st));
+                std::vector<double2> hh((size_t)nr * FB);
+                OV_TRY(to_host(c, c->dscal, hh.data(), hh.size() * sizeof(double2), st));
+                for (int j = j0; j < std::min(j0 + FB, nr); ++j)
+                    for (int i = 0; i < nr; ++i) {
+                        const double2 v = hh[(size_t)i * FB + (j - w0)];
+                        M[(size_t)i * nr + j] = cd(v.x, v.y);
+                    }
             }
             for (int i = 0; i < nr; ++i)
                 for (int j = i; j < nr; ++j) {
@@ -499,16 +556,23 @@ int chfsi(ov_ctx* c, const OpFn& A, const OpFn& Awork, const OpFn& R, int K, dou
             OV_TRY(rotate(c, V, nr, So, nr, nr, eta, W.zero, st));
             int good = 0;
             maxres = 0;
-            for (int j = 0; j < nr; ++j) {
-                OV_TRY(R(sub(eta, j), W.w));
-                FieldDesc xs[2] = {W.w, sub(eta, j)};
-                const double2 h2[2] = {make_double2(1, 0), make_double2(-lo[j], 0)};
-                OV_TRY(lincomb(c, W.w, 2, xs, h2, nullptr, 0, nullptr, st));
-                const double r = host_norm(c, W.w, st, &status) / rscale;
-                OV_TRY(status);
-                if (r > tol) break;
-                maxres = std::max(maxres, r);
-                ++good;
+            bool bad = false;
+            for (int j0 = 0; j0 < nr && !bad; j0 += FB) {
+                // windows inside W.rot (nb vectors; past nr it holds earlier, finite rotations)
+                const int w0 = std::max(0, std::min(j0, nb - FB));
+                std::vector<double> lw(FB, 0.0);
+                for (int q = 0; q < FB; ++q)
+                    if (w0 + q < nr) lw[q] = lo[w0 + q];
+                OV_TRY(residual_window(R, W.rot, w0, lw.data(), FB));
+                for (int j = j0; j < std::min(j0 + FB, nr); ++j) {
+                    const double r = rwin[j - w0] / rscale;
+                    if (r > tol) {
+                        bad = true;
+                        break;
+                    }
+                    maxres = std::max(maxres, r);
+                    ++good;
+                }
             }
             if (verbose())
                 fprintf(stderr, "[ov] chfsi chi=%d: Rayleigh-Ritz over %d locked vectors, %d good (want %d)\n", chi, nr,
@@ -582,7 +646,7 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     const int oprec = c->eig_prec >= 0 ? c->eig_prec : (tol >= 1e-5 ? P_F32 : c->hi_prec);
 
     LanczosWork W{};
-    FieldDesc outv{}, ta{};
+    FieldDesc outv{};
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);
         field_free(c, &W.basis);
@@ -602,22 +666,19 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     DF_TRY(field_alloc(c, P_F64, nsec * ns, &outv));
     DF_TRY(ws_field(c, WS_AUX1, P_F64, 16, &W.zero));
     DF_TRY(ws_field(c, WS_LZ_W, P_F64, 1, &W.w));
-    DF_TRY(ws_field(c, WS_LZ_T, P_F64, 1, &ta));
+    const int FB = std::min(12, nb);  // filter batch: as many right-hand sides as a propagator solve
+    DF_TRY(ws_field(c, WS_LZ_WB, P_F64, FB, &W.wb));
+    // windows of FB vectors may reach past the rotated vectors of W.rot: keep them finite
+    OV_CUDA(c, cudaMemsetAsync(W.rot.data, 0, W.rot.rhs_bytes() * nb, st));
     OV_CUDA(c, cudaMemsetAsync(W.zero.data, 0, W.zero.rhs_bytes() * 16, st));
     // Operator precision `cur`: the filter temporaries (slots of their own: the Clenshaw buffers
     // are used inside D^dag D) and, below FP64, conversion fields (in, out, middle).
     int cur = oprec;
-    FieldDesc cva[NPREC] = {}, cvb[NPREC] = {}, cvc[NPREC] = {};
     auto prepare = [&](int p) -> int {
-        OV_TRY(ws_field(c, WS_LZ_F0, p, 1, &W.tmp[0]));
-        OV_TRY(ws_field(c, WS_LZ_F1, p, 1, &W.tmp[1]));
-        OV_TRY(ws_field(c, WS_LZ_F2, p, 1, &W.tmp[2]));
-        OV_TRY(ws_field(c, WS_LZ_F3, p, 1, &W.tmp[3]));
-        if (p != P_F64) {
-            OV_TRY(ws_field(c, WS_CG_RS, p, 1, &cva[p]));
-            OV_TRY(ws_field(c, WS_CG_QS, p, 1, &cvb[p]));
-            OV_TRY(ws_field(c, WS_LZ_T, p, 1, &cvc[p]));
-        }
+        OV_TRY(ws_field(c, WS_LZ_F0, p, FB, &W.tmp[0]));
+        OV_TRY(ws_field(c, WS_LZ_F1, p, FB, &W.tmp[1]));
+        OV_TRY(ws_field(c, WS_LZ_F2, p, FB, &W.tmp[2]));
+        OV_TRY(ws_field(c, WS_LZ_F3, p, FB, &W.tmp[3]));
         return OV_OK;
     };
     DF_TRY(prepare(oprec));
@@ -633,20 +694,26 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     double bmax, rscale;
     int K;
     if (which == 0) {
-        Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int {
-            const FieldDesc& tmid = cur == P_F64 ? ta : cvc[cur];
+        Awork = [&](const FieldDesc& in, const FieldDesc& out) -> int {  // the filter's batch
+            FieldDesc tmid;
+            OV_TRY(ws_field(c, WS_LZ_T, cur, in.nrhs, &tmid));
             OV_TRY(dslash_apply(c, in, tmid, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
             return dslash_apply(c, tmid, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
         };
-        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {  // one vector or a window of FB
+            FieldDesc t;
+            OV_TRY(ws_field(c, WS_LZ_T, cur, in.nrhs, &t));
             if (cur == P_F64) {
-                OV_TRY(dslash_apply(c, in, ta, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-                return dslash_apply(c, ta, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
+                OV_TRY(dslash_apply(c, in, t, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+                return dslash_apply(c, t, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
             }
-            OV_TRY(convert(c, in, cva[cur], st));
-            OV_TRY(dslash_apply(c, cva[cur], cvc[cur], 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-            OV_TRY(dslash_apply(c, cvc[cur], cvb[cur], 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
-            return convert(c, cvb[cur], out, st);
+            FieldDesc a, b;
+            OV_TRY(ws_field(c, WS_CG_RS, cur, in.nrhs, &a));
+            OV_TRY(ws_field(c, WS_CG_QS, cur, in.nrhs, &b));
+            OV_TRY(convert(c, in, a, st));
+            OV_TRY(dslash_apply(c, a, t, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            OV_TRY(dslash_apply(c, t, b, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st));
+            return convert(c, b, out, st);
         };
         R = [&](const FieldDesc& in, const FieldDesc& out) -> int {
             return dslash_apply(c, in, out, 4.0 - c->rho, -0.5, 1, 0, 0, nullptr, nullptr, st);
@@ -661,15 +728,20 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         K = c->filter_hw;
     } else {
         // D^dag D, or with the "chiral" option its one-sign form on the sector being solved
+        // (coefficients [3][R]: at dchi for one vector, at dchi + 8 for the filter's batch)
         const double2* dchi = (const double2*)(c->dscal + DSCAL_CHCO);
         Awork = [&, dchi](const FieldDesc& in, const FieldDesc& out) -> int {
-            return c->chiral ? chiral_apply(c, in, out, 0.0, dchi, st) : normal_apply(c, in, out, 0.0, st);
+            const double2* dc = in.nrhs == 1 ? dchi : dchi + 8;
+            return c->chiral ? chiral_apply(c, in, out, 0.0, dc, st) : normal_apply(c, in, out, 0.0, st);
         };
-        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {
+        A = [&](const FieldDesc& in, const FieldDesc& out) -> int {  // one vector or a window of FB
             if (cur == P_F64) return Awork(in, out);
-            OV_TRY(convert(c, in, cva[cur], st));
-            OV_TRY(Awork(cva[cur], cvb[cur]));
-            return convert(c, cvb[cur], out, st);
+            FieldDesc a, b;
+            OV_TRY(ws_field(c, WS_CG_RS, cur, in.nrhs, &a));
+            OV_TRY(ws_field(c, WS_CG_QS, cur, in.nrhs, &b));
+            OV_TRY(convert(c, in, a, st));
+            OV_TRY(Awork(a, b));
+            return convert(c, b, out, st);
         };
         R = A;
         bmax = 4.0 * c->rho * c->rho * 1.01;
@@ -685,6 +757,10 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
         if (which == 1 && c->chiral) {
             const double2 hc[3] = {make_double2(0, 0), make_double2(c->rho, 0), make_double2(chi * c->rho, 0)};
             DF_TRY(to_dev(c, hc, c->dscal + DSCAL_CHCO, sizeof hc, st));
+            std::vector<double2> hb(3 * FB);
+            for (int k = 0; k < 3; ++k)
+                for (int q = 0; q < FB; ++q) hb[k * FB + q] = hc[k];
+            DF_TRY(to_dev(c, hb.data(), c->dscal + DSCAL_CHCO + 16, hb.size() * sizeof(double2), st));
         }
         std::vector<double> v;
         double mr = 0;
@@ -1102,7 +1178,6 @@ int multimass_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc* xout, int 
     OV_TRY(ws_field(c, WS_CG_PS, Ps, R, &p));
     OV_TRY(ws_field(c, WS_CG_QS, Ps, R, &q));
     std::vector<FieldDesc> pk(M), yk(M);
-    int status = OV_OK;
     auto release = [&]() {
         cudaStreamSynchronize(st);
         for (auto& f : pk) field_free(c, &f);
@@ -1386,7 +1461,6 @@ int rational_solve(ov_ctx* c, const FieldDesc& src, const FieldDesc& s, int gpre
     };
     const bool single = c->rational_pass == 1;
     std::vector<FieldDesc> xs, ps;
-    int status = OV_OK;
     auto release = [&]() {
         cudaStreamSynchronize(st);
         for (auto& f : xs) field_free(c, &f);
