@@ -87,6 +87,21 @@ int ws_field(ov_ctx* c, int slot, int prec, int nrhs, FieldDesc* f)
     return OV_OK;
 }
 
+// Free every cached work field of `slot` (of precision `prec` and `nrhs` right-hand sides; -1: any).
+// Captured graphs may hold their addresses: the caller clears the graphs first.
+void ws_release(ov_ctx* c, int slot, int prec, int nrhs)
+{
+    for (auto it = c->ws.begin(); it != c->ws.end();) {
+        const auto& k = it->first;
+        if (std::get<0>(k) == slot && (prec < 0 || std::get<1>(k) == prec) && (nrhs < 0 || std::get<2>(k) == nrhs)) {
+            field_free(c, &it->second);
+            it = c->ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 int ensure_partials(ov_ctx* c, size_t bytes)
 {
     if (bytes <= c->partials_bytes) return OV_OK;
@@ -347,7 +362,9 @@ static int overlap_core(ov_ctx* c, const FieldDesc& in, const FieldDesc& out, do
             OV_CUDA(c, launch_proj_dots(c->g, eta, E.nev, in, (double2*)c->partials, nblk, st));
             OV_CUDA(c, launch_proj_finalize((double2*)c->partials, nparts, (int)ncoef, dcoef, st));
         }
-        if (tc)
+        // the update of one FP32 right-hand side streams the rows once on the CUDA cores, faster than the
+        // tensor cores' rows plus remainder rows (measured 0.24 against 0.32 ms at 16^3 x 32, 100 rows)
+        if (tc && !(P == P_F32 && R == 1))
             OV_TRY(proj_update_tc(c, 0, in, dcoef, E.d_sign, ph, w, st));
         else
             OV_CUDA(c, launch_proj_update(c->g, eta, E.nev, dcoef, E.d_sign, in, ph, w, st));

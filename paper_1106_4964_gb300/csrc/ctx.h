@@ -154,6 +154,7 @@ void dev_free(ov_ctx* c, void* p, size_t bytes);
 int field_alloc(ov_ctx* c, int prec, int nrhs, FieldDesc* f);
 void field_free(ov_ctx* c, FieldDesc* f);
 int ws_field(ov_ctx* c, int slot, int prec, int nrhs, FieldDesc* f);
+void ws_release(ov_ctx* c, int slot, int prec = -1, int nrhs = -1);
 int ensure_partials(ov_ctx* c, size_t bytes);
 bool is_device_ptr(const void* p);
 int stage_in(ov_ctx* c, int which, const void* src, size_t bytes, cudaStream_t st, const double** dev);

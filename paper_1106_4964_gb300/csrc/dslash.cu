@@ -9,7 +9,8 @@ cudaError_t launch_dslash(const DslashArgs& A, int sp, int gp, int ny, int bx, i
 {
     if (bx <= 0 || by <= 0 || bx * by > (wide(sp) ? 256 : 512)) return cudaErrorInvalidValue;
     const dim3 block(bx, by);
-    const dim3 grid(2 * ((A.g.Vh + bx - 1) / bx), (A.nrhs + by - 1) / by);
+    // one dimension: 2 parities x site blocks x right-hand-side groups (the kernels' block_work)
+    const dim3 grid((unsigned)(2 * ((A.g.Vh + bx - 1) / bx) * ((A.nrhs + by - 1) / by)));
     if (var >= 0 && var <= 2) return launch_dslash_regs(A, sp, gp, ny, var, grid, block, st);
     if (var >= 3 && var <= 5) return launch_dslash_staged(A, sp, gp, ny, var, grid, block, st);
     if (var == 6 || var == 7) return launch_dslash_multi(A, sp, gp, ny, var, grid, block, st);

@@ -105,9 +105,10 @@ __device__ __forceinline__ void raw_hop(const RawHop<SP, GP>& R, bool cross, flo
 template <int SP, int GP, int NY, int NB>
 __global__ void __launch_bounds__(128) dslash_batched_kernel(DslashArgs A)
 {
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const BlockWork bw = block_work((A.nrhs + blockDim.y - 1) / blockDim.y);
+    const int p = bw.p;
+    const int s = bw.sb * blockDim.x + threadIdx.x;
+    const int r = bw.grp * blockDim.y + threadIdx.y;
     const Geom& g = A.g;
     if (s >= g.Vh || r >= A.nrhs) return;
     constexpr size_t CH = nchunk_dev<SP>() * 16;

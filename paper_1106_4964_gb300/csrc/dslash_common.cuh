@@ -4,12 +4,14 @@
 //                 - 1/2 sum_mu [ U_mu(n) (1 - gamma_mu) psi(n + mu)
 //                              + U_mu(n - mu)^dag (1 + gamma_mu) psi(n - mu) ]
 //
-// One launch computes both parities of the output: block b handles parity
-// b & 1 and checkerboard sites [(b >> 1) * BX, +BX), so the two parities of
-// the same region run together and the links and neighbour spinors one
-// parity reads are re-read by the other while they sit in L2.  Threads
-// (x, y) of a block handle site x of right-hand side blockIdx.y*BY + y; the
-// BY right-hand sides of a block share every link load through L1.
+// One launch computes both parities of the output and all right-hand sides.
+// Blocks are numbered with the right-hand-side group fastest, then the parity,
+// then the site block (block_work below): the groups and both parities of one
+// region of BX checkerboard sites run back to back, so the links and
+// neighbour spinors they share are re-read from L2, not from HBM once per
+// group.  Threads (x, y) of a block handle site x of right-hand side
+// group * BY + y; the BY right-hand sides of a block share every link load
+// through L1.
 //
 // Spin structure (Euclidean chiral basis, gamma_mu = [[0, A_mu], [A_mu^dag, 0]],
 // A_k = -i sigma_k, A_4 = 1): (1 - S gamma_mu) psi has upper half
@@ -198,13 +200,27 @@ struct Bounds {
     static constexpr int minb = VAR == 0 ? 1 : (wide_dev<SP> ? VAR + 1 : VAR + 2);
 };
 
+// The work of block blockIdx.x in a launch of `ngroups` right-hand-side groups: parity p, site block sb,
+// group grp (grid: 2 x site blocks x ngroups, one dimension)
+struct BlockWork {
+    int p, sb, grp;
+};
+__device__ __forceinline__ BlockWork block_work(int ngroups)
+{
+    const int b = (int)blockIdx.x;
+    if (ngroups == 1) return {b & 1, b >> 1, 0};
+    const int rest = b / ngroups;
+    return {rest & 1, rest >> 1, b - rest * ngroups};
+}
+
 template <int SP, int GP, int NY, int VAR>
 __global__ void __launch_bounds__(Bounds<SP, VAR>::maxt, Bounds<SP, VAR>::minb) dslash_kernel(DslashArgs A)
 {
     using Real = real_t<SP>;
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const BlockWork bw = block_work((A.nrhs + blockDim.y - 1) / blockDim.y);
+    const int p = bw.p;
+    const int s = bw.sb * blockDim.x + threadIdx.x;
+    const int r = bw.grp * blockDim.y + threadIdx.y;
     const Geom& g = A.g;
     if (s >= g.Vh || r >= A.nrhs) return;
 
@@ -268,6 +284,12 @@ __device__ __forceinline__ void epilogue(const DslashArgs& A, int r, int p, int 
         for (int i = 12; i < 24; ++i) o[i] = -o[i];
     }
     store_spinor<SP, Real>(A.out + off, A.out_n ? A.out_n + noff : nullptr, g.Vh, s, o);
+}
+
+// Host side of block_work: the one-dimensional grid of a launch with site blocks of bx sites
+inline dim3 block_grid(int Vh, int bx, int ngroups)
+{
+    return dim3((unsigned)(2 * ((Vh + bx - 1) / bx) * ngroups));
 }
 
 // One launcher per precision pair: G::run<SP, GP> for the seven supported (spinor, link) formats.

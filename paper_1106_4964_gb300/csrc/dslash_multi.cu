@@ -11,7 +11,7 @@ namespace {
 // row reconstructed once per RB right-hand sides instead of once per
 // right-hand side (the multi-RHS launch is bound by instruction issue, and the
 // link work is a fifth of it).  Threads (x, y): site x of the block's range,
-// right-hand sides RB * (blockIdx.y * BY + y) + j, j < RB.
+// right-hand sides RB * (group * BY + y) + j, j < RB (block_work numbers the groups).
 // ---------------------------------------------------------------------------
 template <int SP, int GP, int MU, int S, int RB>
 __device__ __forceinline__ void hop_multi(const DslashArgs& A, const char* const in_q[RB], const float* const inn_q[RB],
@@ -42,9 +42,11 @@ __device__ __forceinline__ void hop_multi(const DslashArgs& A, const char* const
 template <int SP, int GP, int NY, int RB>
 __global__ void __launch_bounds__(128) dslash_multi_kernel(DslashArgs A)
 {
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * RB;
+    const int ngroups = ((A.nrhs + RB - 1) / RB + blockDim.y - 1) / blockDim.y;
+    const BlockWork bw = block_work(ngroups);
+    const int p = bw.p;
+    const int s = bw.sb * blockDim.x + threadIdx.x;
+    const int r0 = (bw.grp * blockDim.y + threadIdx.y) * RB;
     const Geom& g = A.g;
     if (s >= g.Vh || r0 >= A.nrhs) return;
     const int nr = A.nrhs - r0 < RB ? A.nrhs - r0 : RB;
@@ -87,7 +89,7 @@ cudaError_t launch_multi(const DslashArgs& A, int ny, dim3 block, cudaStream_t s
     } else {
         if ((int)(block.x * block.y) > 128) return cudaErrorInvalidValue;
         const int groups = (A.nrhs + RB - 1) / RB;
-        const dim3 grid(2 * ((A.g.Vh + block.x - 1) / block.x), (groups + block.y - 1) / block.y);
+        const dim3 grid = block_grid(A.g.Vh, block.x, (groups + block.y - 1) / block.y);
         switch (ny) {
         case 0: dslash_multi_kernel<SP, GP, 0, RB><<<grid, block, 0, st>>>(A); break;
         case 1: dslash_multi_kernel<SP, GP, 1, RB><<<grid, block, 0, st>>>(A); break;

@@ -156,9 +156,11 @@ template <int SP, int GP, int NY, int NP>
 __global__ void __launch_bounds__(128) dslash_pair_kernel(DslashArgs A)
 {
     constexpr int RB = 2 * NP;
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * blockDim.x + threadIdx.x;
-    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * RB;
+    const int ngroups = ((A.nrhs + RB - 1) / RB + blockDim.y - 1) / blockDim.y;
+    const BlockWork bw = block_work(ngroups);
+    const int p = bw.p;
+    const int s = bw.sb * blockDim.x + threadIdx.x;
+    const int r0 = (bw.grp * blockDim.y + threadIdx.y) * RB;
     const Geom& g = A.g;
     if (s >= g.Vh || r0 >= A.nrhs) return;
     const int nr = A.nrhs - r0 < RB ? A.nrhs - r0 : RB;
@@ -209,7 +211,7 @@ cudaError_t launch_pair(const DslashArgs& A, int ny, dim3 block, cudaStream_t st
     } else {
         if ((int)(block.x * block.y) > 128) return cudaErrorInvalidValue;
         const int groups = (A.nrhs + 2 * NP - 1) / (2 * NP);
-        const dim3 grid(2 * ((A.g.Vh + block.x - 1) / block.x), (groups + block.y - 1) / block.y);
+        const dim3 grid = block_grid(A.g.Vh, block.x, (groups + block.y - 1) / block.y);
         switch (ny) {
         case 0: dslash_pair_kernel<SP, GP, 0, NP><<<grid, block, 0, st>>>(A); break;
         case 1: dslash_pair_kernel<SP, GP, 1, NP><<<grid, block, 0, st>>>(A); break;

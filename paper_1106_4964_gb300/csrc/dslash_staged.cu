@@ -136,9 +136,10 @@ __global__ void __launch_bounds__(128) dslash_staged_kernel(DslashArgs A)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int BX = blockDim.x, tx = threadIdx.x;
-    const int p = blockIdx.x & 1;
-    const int s = (blockIdx.x >> 1) * BX + tx;
-    const int r = blockIdx.y;
+    const BlockWork bw = block_work(A.nrhs);  // one right-hand side per block
+    const int p = bw.p;
+    const int s = bw.sb * BX + tx;
+    const int r = bw.grp;
     const Geom& g = A.g;
     if (s >= g.Vh || r >= A.nrhs) return;
     constexpr size_t CH = nchunk_dev<SP>() * 16;
@@ -197,7 +198,7 @@ cudaError_t launch_staged(const DslashArgs& A, int ny, dim3 grid, dim3 block, cu
             if (e != cudaSuccess) return e;
             attr_set[ny] = true;
         }
-        dim3 g2(grid.x, A.nrhs);
+        const dim3 g2 = block_grid(A.g.Vh, block.x, A.nrhs);
         switch (ny) {
         case 0: dslash_staged_kernel<SP, GP, 0><<<g2, block, shm, st>>>(A); break;
         case 1: dslash_staged_kernel<SP, GP, 1><<<g2, block, shm, st>>>(A); break;

@@ -773,8 +773,17 @@ int deflate_impl(ov_ctx* c, int which, int nev, double tol, cudaStream_t st)
     for (size_t i = 0; i < pick.size(); ++i) pick[i] = (int)i;
     std::stable_sort(pick.begin(), pick.end(), [&](int a, int b) { return std::fabs(allv[a]) < std::fabs(allv[b]); });
     pick.resize(nev);
+    // the block and its rotation copy go before the eigenvectors' own storage is allocated (at 32^3 x 64
+    // they are 150 GB), then the work fields that only the eigensolver uses
+    cudaStreamSynchronize(st);
+    field_free(c, &W.basis);
+    field_free(c, &W.rot);
     DF_TRY(store_eigs(c, which, outv, pick, allv, st));
     cleanup();
+    graphs_clear(c);  // captured applications may refer to the fields released here
+    for (int slot : {(int)WS_LZ_WB, (int)WS_LZ_T, (int)WS_LZ_F0, (int)WS_LZ_F1, (int)WS_LZ_F2, (int)WS_LZ_F3})
+        ws_release(c, slot);
+    ws_release(c, WS_AUX1, P_F64, 16);
 #undef DF_TRY
     (void)worst;
     return OV_OK;
@@ -899,22 +908,29 @@ int cg_impl(ov_ctx* c, const FieldDesc& b_in, const FieldDesc& x_out, double mas
     // them cannot be solved for, so the true residual is measured on their orthogonal complement
     int nzero = 0;
     for (int i = 0; i < nd; ++i) nzero += inv[i] == 0.0;
+    // x <- x - sum_{zero modes} xi_i (xi_i^dag x): the pseudo-inverse has no component along them, and
+    // the inner precision's rounding would otherwise leave one in the accumulated solution
+    auto drop_zero_modes = [&](const FieldDesc& v) -> int {
+        OV_TRY(block_dots(c, xi64, nd, v, st));
+        std::vector<double2> h((size_t)nd * R);
+        OV_TRY(to_host(c, c->dscal, h.data(), h.size() * sizeof(double2), st));
+        for (int i = 0; i < nd; ++i)
+            if (inv[i] != 0.0)
+                for (int q = 0; q < R; ++q) h[(size_t)i * R + q] = make_double2(0, 0);
+        OV_TRY(to_dev(c, h.data(), c->dscal, h.size() * sizeof(double2), st));
+        FieldDesc none{};
+        OV_CUDA(c, launch_proj_update(c->g, xi64, nd, (const double2*)c->dscal, nullptr, v, v, none, st));
+        return OV_OK;
+    };
     auto refresh = [&](bool& all_done) -> int {
+        if (nzero) OV_TRY(drop_zero_modes(x));
         OV_TRY(normal_apply(c, x, t, mass, st));
         FieldDesc v2[2] = {b, t};
         double2 h2[2] = {make_double2(1, 0), make_double2(-1, 0)};
         OV_TRY(lincomb(c, r, 2, v2, h2, nullptr, 0, dnr, st));
         std::vector<double> nr(R);
         if (nzero) {
-            OV_TRY(block_dots(c, xi64, nd, r, st));
-            std::vector<double2> h((size_t)nd * R);
-            OV_TRY(to_host(c, c->dscal, h.data(), h.size() * sizeof(double2), st));
-            for (int i = 0; i < nd; ++i)
-                if (inv[i] != 0.0)
-                    for (int q = 0; q < R; ++q) h[(size_t)i * R + q] = make_double2(0, 0);
-            OV_TRY(to_dev(c, h.data(), c->dscal, h.size() * sizeof(double2), st));
-            FieldDesc none{};
-            OV_CUDA(c, launch_proj_update(c->g, xi64, nd, (const double2*)c->dscal, nullptr, r, r, none, st));
+            OV_TRY(drop_zero_modes(r));
             std::vector<double2> hn(R);
             OV_TRY(norm2(c, r, (double*)ddt, st));
             OV_TRY(to_host(c, ddt, hn.data(), R * sizeof(double2), st));
