@@ -98,6 +98,7 @@ def test_train_and_flexible_cg():
     curve = ctx.net_loss_history()  # before each of the 60 Adam steps, and after the last
     assert len(curve) == 61 and curve[-1] == pytest.approx(loss, rel=1e-12)
     assert curve[-1] < curve[0]
+    print("net loss curve (step: loss per pair): " + ", ".join(f"{i}: {curve[i]:.4f}" for i in range(0, 61, 6)))
     b = synth.gaussian_spinor(cf["dims"], 12)
     x = torch.empty_like(dev(b))
     plain = ctx.cg_solve(dev(b), x, mass=mass, tol=1e-10, max_iter=3000, inner_prec="f32")
