@@ -73,8 +73,9 @@ typedef struct {
                                 halve the true residual), the solve continued with the two-sign operator */
     int nrhs;
     double true_residual[64]; /* ||b - A x|| / ||b|| by the FP64 operator, per rhs; with exact
-                                 zero modes among the stored D^dag D modes (massless, excluded
-                                 from x) it is measured on their orthogonal complement */
+                                 zero modes among the stored D^dag D modes (massless: x carries no
+                                 component along them) it is measured on their orthogonal
+                                 complement */
     double seconds;          /* wall time of the solve */
 } ov_solve_info;
 
@@ -325,7 +326,12 @@ int ov_measure_fma_peak(int prec, double* gflops, void* stream);
  *                    instead of two (equal up to the polynomial's error; the true
  *                    residuals keep the full operator); every right-hand side
  *                    must satisfy gamma5 b = chi b, else OV_EINVAL (point
- *                    sources do).  ov_deflate(1) uses the same operator per sector;
+ *                    sources do).  Where the sign's delta couples the sectors by
+ *                    more than the tolerance allows the solve switches to the
+ *                    two-sign operator (ov_solve_info.fallback bit 2); a sign
+ *                    with delta well below the tolerance ("sign_delta" of
+ *                    ov_get_option) avoids that.  ov_deflate(1) uses the same
+ *                    operator per sector;
  *   "hi_prec" (OV_F64): precision of the accurate arithmetic in ov_cg_solve
  *                    (true residuals, solution accumulation) and of the
  *                    automatic ov_deflate operator: OV_F64 or OV_DF64;
